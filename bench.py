@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: the relaxing-TVD MHD step on a 512^3 magnetised blast wave
+(periodic unit cube, gamma 5/3, rho 1, p 10 inside r < 0.1 else 0.1, B = (1,1,0)/sqrt(2)),
+FP32 sweeps with FP64 conservation sums every 10 steps.
+
+One "step" is one full method step (dt from the CFL condition, forward and reverse
+dimensionally split sweeps, 6 fluid + 6 constrained-transport operators), advancing
+every cell once: the metric counts cell-updates per second.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--n 512]
+
+N > 1 (under torchrun): independent replicas, one grid per GPU (the path needs no data
+exchange between grids); value = cells x steps summed over ranks / max time over ranks.
+--impl reference: the FP64 CPU oracle on the host cores, timed on a bounded sample of the
+same workload (rank 0 only).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (512³ FP32) & %HBM roofline vs FP64; batched p50/p99 latency"
+UNIT = "cell-updates/s"
+SUMS_EVERY = 10
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes per cell for one launch of each kernel kind (FP32): the fields the
+# operator must read and write once.  fluid: reads 8 fields, writes 5; CT: reads rho, m_n
+# and the 3 B components, writes 3.  The method step (6 L-ops x 8 fields read + written)
+# is 384 B per cell.
+ALG_BYTES = {"fluid": 13 * 4, "ct": 8 * 4}
+STEP_ALG_BYTES = 384
+# DRAM traffic per cell of one fluid-sweep launch from an ncu capture, keyed by the hash of
+# the kernel source it was taken on (None until captured); stale hashes report null.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mhd_kernels.cuh", "mhd_launch_impl.cuh"):
+        with open(os.path.join(ROOT, "paper_0908_4362_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def workload_config(n: int) -> dict:
+    return {"workload": f"3D magnetised blast wave {n}^3, periodic unit cube, gamma 5/3, "
+                        f"p 10 in r<0.1 else 0.1, B=(1,1,0)/sqrt(2), FP32 sweeps, FP64 "
+                        f"conservation sums every {SUMS_EVERY} steps",
+            "grid": [n, n, n], "cells": n ** 3, "cfl": 0.7,
+            "l2": "inputs larger than L2 (8 FP32 fields x 2 buffers, no flush needed)"}
+
+
+def measured_peaks() -> tuple:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str | None):
+        self.dev_id = dev_id
+        self.proc = None
+        self.lines: list = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.dev_id:
+            cmd += ["-i", self.dev_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                  "sw_power_cap"), parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a host float over ranks (timing reduction only; no data-path collective)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on the host cores
+# ------------------------------------------------------------------------------------
+
+def oracle_sample(n: int, edge: int, steps: int) -> dict:
+    """Time the FP64 oracle (OpenMP, all host cores) for `steps` steps on an edge^3 cut of
+    the n^3 blast workload centred on the blast (periodic cut)."""
+    import numpy as np
+
+    import oracle
+    from paper_0908_4362_gb300 import inputs as I
+    edge = min(edge, n)
+    # the cut keeps the full workload's cell width and blast radius
+    h = 1.0 / n
+    c = (np.arange(edge) - edge / 2 + 0.5) * h
+    r2 = c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2
+    p = np.where(r2 < 0.01, 10.0, 0.1)
+    z = np.zeros((edge,) * 3)
+    f = I.conserved(np.ones((edge,) * 3), [z, z, z], p,
+                    [np.full(z.shape, 1 / 2 ** 0.5), np.full(z.shape, 1 / 2 ** 0.5), z],
+                    5.0 / 3.0, (0, 0, 0))
+    o = oracle.Oracle((edge,) * 3, (0, 0, 0), h, 5.0 / 3.0, 0.7, f)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    cells = edge ** 3 * steps
+    return {"value": cells / dt, "unit": UNIT, "seconds": dt,
+            "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+            "kind": "oracle",
+            "sample": f"{steps} step(s) of an {edge}^3 cut (cell width 1/{n}) of the {n}^3 "
+                      f"blast workload, FP64 oracle, OpenMP over pencils"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    edge = args.ref_edge
+    oracle_sample(args.n, edge, 1)          # build + warm caches
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_sample(args.n, edge, 1)
+    t0 = time.perf_counter()
+    res = None
+    tot = 0.0
+    for _ in range(args.steps):
+        res = oracle_sample(args.n, edge, 1)
+        tot += res["seconds"]
+    value = edge ** 3 * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_0908_4362_gb300 import build, mhd
+    from paper_0908_4362_gb300 import inputs as I
+
+    build.build()
+    torch.cuda.set_device(local)
+    n = args.n
+    prob = I.blast3d(n)
+    N = prob.ncells
+    # pinned FP32 host copies of the initial state (the e2e inputs)
+    host = [torch.from_numpy(prob.fields[k].astype(np.float32)).pin_memory() for k in range(8)]
+    del prob.fields
+    solver = mhd.Solver((n, n, n), (0, 0, 0), 1.0 / n, 5.0 / 3.0, 0.7, prec=mhd.FP32)
+    solver.upload(host)
+    solver.step(args.warmup, sync=True)
+    solver.sums()
+
+    # ---- timed region: device-resident state, kernel-by-kernel with CUDA events ----
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    stream = torch.cuda.ExternalStream(solver.stream_handle())
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dev_uuid = None
+    try:
+        dev_uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(dev_uuid)
+    torch.cuda.synchronize()
+    solver.sync()
+    barrier(world)
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    sums_calls = 0
+    for k in range(args.steps):
+        solver.step(1)
+        if (k + 1) % SUMS_EVERY == 0:
+            solver.sums()
+            sums_calls += 1
+    ev1.record(stream)
+    ev1.synchronize()
+    solver.sync()
+    barrier(world)
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = solver.profile_read(reset=True)
+    solver.profile(False)
+    max_ms = max_over_ranks(ms_total, world)
+    total_cells = sum_over_ranks(float(N) * args.steps, world)
+    value = total_cells / (max_ms / 1e3)
+
+    # roofline of the dominant kernel kind (by total time), algorithmic bytes / duration
+    kinds = {}
+    for name, (ms, cnt) in prof.items():
+        base = name.split("_")[0]
+        if base in ALG_BYTES and cnt:
+            kms, kc = kinds.get(base, (0.0, 0))
+            kinds[base] = (kms + ms, kc + cnt)
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_cnt = kinds[dom]
+    avg_ms = dom_ms / dom_cnt
+    achieved = ALG_BYTES[dom] * N / (avg_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    src_hash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(src_hash)
+    launches = sum(c for _, c in prof.values()) + 2 * sums_calls
+
+    # ---- e2e: through the C ABI with pinned host buffers, copies inside the region ----
+    e2e = None
+    if not args.no_e2e:
+        out = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(8)]
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        solver.upload(host)
+        solver.step(args.steps)
+        solver.download(out)
+        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(e2e_s, world)
+        nb = 8 * N * 4
+        e2e = {"value": total_cells / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": nb / args.steps, "d2h_bytes_per_step": nb / args.steps,
+               "note": f"one job per rank: upload of the 8 FP32 fields from pinned host memory, "
+                       f"{args.steps} steps, download of the 8 fields to pinned host memory"}
+    solver.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(n, args.cpu_edge, 1)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        step_ms = max_ms / args.steps
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": workload_config(n),
+                "roofline": {"bound": "hbm", "kernel": f"{dom} sweep (all axes)",
+                             "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_src,
+                             "traffic": traffic, "alg_bytes_per_cell": ALG_BYTES[dom],
+                             "avg_launch_ms": avg_ms, "kernel_source": src_hash},
+                "step_roofline": {"alg_bytes_per_cell": STEP_ALG_BYTES,
+                                  "achieved": STEP_ALG_BYTES * N / (step_ms / 1e3) / 1e9,
+                                  "frac": STEP_ALG_BYTES * N / (step_ms / 1e3) / 1e9 / peak},
+                "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
+                "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--cpu-edge", type=int, default=256)
+    ap.add_argument("--ref-edge", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,144 @@
+/*
+ * mhd.h - C ABI of the GB300 relaxing-TVD ideal-MHD solver.
+ *
+ * Method: Wong, Wong, Feng & Tang, "Efficient magnetohydrodynamic simulations on graphics
+ * processing units with CUDA" (arXiv:0908.4362).  The solver advances the ideal MHD
+ * equations (Sect. 3, equations of the conservation laws, mu = 1) on a regular Cartesian
+ * grid with the relaxing-TVD scheme (Sect. 3), constrained transport for B (Sect. 3,
+ * Eqs. "eq:averaging_x", "eq:first_flux"), dimensionally split forward and reverse sweeps
+ * with a cycled axis order (Eq. "eq:L_sequence"), and a CFL time step (Eq. "equat_CFL").
+ * All arithmetic runs in the library's CUDA kernels on one GPU (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *   Fields      8 arrays in the order (rho, rho*vx, rho*vy, rho*vz, E, Bx, By, Bz)
+ *               (Sect. 4.1, "eight components ... stored in eight arrays").
+ *   Index       cell (x, y, z) is element (x*ny + y)*nz + z of each array: z is contiguous
+ *               (Sect. 4.1, index equations).
+ *   Staggering  B is face centred (Eq. "equat_b"): Bx[x,y,z] lives on the x-face x-1/2,
+ *               By on the y-face y-1/2, Bz on the z-face z-1/2.  Cell width h on all axes.
+ *   Boundaries  per axis, periodic (wrap) or outflow (every array index clamped to the
+ *               grid, i.e. zero-gradient ghost cells).  The paper does not specify them.
+ *   Step        one step = dt from the CFL condition, forward sweep L_c L_b L_a and
+ *               reverse sweep L_a L_b L_c, t += 2 dt, axis order (a,b,c) cycled over
+ *               (x,y,z), (z,x,y), (y,z,x) (Sect. 4.2 steps 4-8, Eq. "eq:L_sequence").
+ *   Ownership   the context owns all device memory; host and device buffers passed in are
+ *               owned by the caller, only read or written during the call (or, for the
+ *               asynchronous calls, until the context's stream reaches that point).
+ *   Errors      every call returns a status and never aborts.  Device-side problems
+ *               (rho <= 0, a negative fast-speed radicand, non-finite values, bad dt) are
+ *               sticky bits in the context, reported by the next call that synchronises
+ *               (mhd_read, mhd_sums, mhd_state, mhd_step with a non-NULL out pointer).
+ *   Threads     a context may be used from one host thread at a time.
+ */
+#ifndef MHD_GB300_H
+#define MHD_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhd_ctx mhd_ctx;
+
+typedef enum {
+  MHD_OK = 0,
+  MHD_ERR_INVALID = 1,     /* bad argument or configuration */
+  MHD_ERR_OOM = 2,         /* device allocation failed */
+  MHD_ERR_CUDA = 3,        /* a CUDA call failed (the message is in mhd_last_error) */
+  MHD_ERR_UNPHYSICAL = 4,  /* rho <= 0, NaN/Inf, or gamma p/rho + B^2/rho < 0 seen */
+  MHD_ERR_TIMEOUT = 5      /* a bounded device wait gave up (batched form) */
+} mhd_status;
+
+typedef enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 } mhd_bc;
+typedef enum { MHD_FP32 = 0, MHD_FP64 = 1 } mhd_precision;
+
+typedef struct {
+  int nx, ny, nz;        /* cells per axis, each >= 1 */
+  double h;              /* cell width, > 0 (the paper uses h = 1) */
+  double gamma;          /* ratio of specific heats, > 1 */
+  double cfl;            /* Courant number, 0 < cfl < 1 (paper: ~0.7) */
+  int bc[3];             /* mhd_bc per axis */
+  int prec;              /* mhd_precision of the device state and arithmetic */
+  int fp64_pressure;     /* FP32 only: recover p = (gamma-1)(E - rho v^2/2 - B^2/2) in FP64 */
+  void* cuda_stream;     /* cudaStream_t to run on; NULL: the context creates its own */
+} mhd_config;
+
+/* Validate cfg and create a context: device state (two buffers per field, the ping-pong
+ * of the out-of-place sweeps), step scalars and scratch.  *out is NULL on failure.
+ * The state is undefined until mhd_init_fields or mhd_upload. */
+mhd_status mhd_create(const mhd_config* cfg, mhd_ctx** out);
+
+/* Load the state from 8 host arrays of nx*ny*nz doubles (copied; converted to the
+ * context precision), set t = t0, step = 0, phase = 0, clear the status and compute the
+ * CFL speed of the new state (Sect. 4.2 steps 2-4).  Blocking. */
+mhd_status mhd_init_fields(mhd_ctx* ctx, const double* const f[8], double t0);
+
+/* As mhd_init_fields, from 8 arrays of dtype (0 = float32, 1 = float64) in host memory
+ * (on_device = 0; page-locked host memory copies at full link speed) or device memory
+ * (on_device = 1).  Blocking. */
+mhd_status mhd_upload(mhd_ctx* ctx, const void* const f[8], int dtype, int on_device, double t0);
+
+/* Advance up to nsteps steps (Sect. 4.2 steps 4-9).  t_end < 0: exactly nsteps steps,
+ * enqueued on the context's stream without a host synchronisation (CUDA-graph replays).
+ * t_end >= 0: stop once t reaches t_end; the last dt is clipped so that t lands on t_end
+ * exactly; the call synchronises periodically to watch t.  If steps_done or t_now is
+ * non-NULL the call synchronises at the end and reports the steps taken and the time. */
+mhd_status mhd_step(mhd_ctx* ctx, int nsteps, double t_end, int* steps_done, double* t_now);
+
+/* Apply one sweep operator with a given dt, for testing: op 0 = fluid_axis (Algorithm 1),
+ * op 1 = CT along axis for both transverse components (Algorithm 2).  Asynchronous. */
+mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt);
+
+/* c_max of the current state (Eq. "equat_CFL").  Blocking. */
+mhd_status mhd_cmax(mhd_ctx* ctx, double* cmax);
+
+/* Copy the state to 8 host arrays of nx*ny*nz doubles.  Blocking; returns the sticky
+ * status. */
+mhd_status mhd_read(mhd_ctx* ctx, double* const f[8]);
+
+/* As mhd_read, into 8 arrays of dtype in host (on_device = 0) or device (1) memory.
+ * Blocking. */
+mhd_status mhd_download(mhd_ctx* ctx, void* const f[8], int dtype, int on_device);
+
+/* FP64 sums over all cells of the 8 fields (conservation diagnostics; the periodic sums
+ * of rho, m, E and of each face component of B are invariants of the scheme).  Blocking. */
+mhd_status mhd_sums(mhd_ctx* ctx, double out[8]);
+
+/* Checkpoint scalars: time, dt of the last step, steps taken, axis-order phase (0..2).
+ * Together with mhd_read they are a complete checkpoint.  Blocking. */
+mhd_status mhd_state(mhd_ctx* ctx, double* t, double* dt_last, int* step, int* phase);
+
+/* Restore checkpoint scalars after mhd_init_fields/mhd_upload of the saved fields. */
+mhd_status mhd_set_state(mhd_ctx* ctx, double t, int step, int phase);
+
+/* Wait for the context's stream; returns the sticky status. */
+mhd_status mhd_sync(mhd_ctx* ctx);
+
+/* Number of cells and the device bytes the context holds (state, scalars, scratch). */
+mhd_status mhd_info(const mhd_ctx* ctx, long long* ncells, long long* device_bytes);
+
+/* Kernel timing mode (enable != 0): steps are launched kernel by kernel, without CUDA
+ * graphs, with a CUDA event pair recorded on the context's stream around each kernel.
+ * Off by default. */
+mhd_status mhd_profile(mhd_ctx* ctx, int enable);
+
+/* Accumulated kernel times (ms) and launch counts of the timing mode, by kind:
+ * 0..2 fluid sweep along x, y, z; 3..5 CT along x, y, z; 6 dt kernel; 7 other.
+ * Synchronises; reset != 0 clears the accumulators after reading. */
+mhd_status mhd_profile_read(mhd_ctx* ctx, double ms[8], long long count[8], int reset);
+
+/* The cudaStream_t the context runs on (its own, or the one given in mhd_config). */
+mhd_status mhd_stream(const mhd_ctx* ctx, void** stream);
+
+/* Free everything the context owns.  NULL is ignored. */
+void mhd_destroy(mhd_ctx* ctx);
+
+const char* mhd_status_str(mhd_status s);
+
+/* Text of the last CUDA or validation error seen by this context (never NULL). */
+const char* mhd_last_error(const mhd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MHD_GB300_H */

@@ -101,12 +101,17 @@ class Oracle:
     (rho, mx, my, mz, E, Bx, By, Bz), flat index (x*ny + y)*nz + z.
     """
 
-    def __init__(self, n, bc, h, gamma, cfl, fields, t=0.0, phase=0, mutant=0, openmp=True):
+    def __init__(self, n, bc, h, gamma, cfl, fields, t=0.0, phase=0, mutant=0, openmp=True,
+                 copy=True):
         self.lib = load(mutant, openmp)
         self.grid = Grid((C.c_int * 3)(*n), (C.c_int * 3)(*bc), float(h), float(gamma),
                          float(cfl))
         self.n = tuple(int(v) for v in n)
-        self.f = np.ascontiguousarray(np.array(fields, dtype=np.float64).reshape(8, -1))
+        if copy:
+            self.f = np.ascontiguousarray(np.array(fields, dtype=np.float64).reshape(8, -1))
+        else:   # advance the caller's float64 array in place
+            self.f = np.asarray(fields, dtype=np.float64).reshape(8, -1)
+            assert self.f.flags["C_CONTIGUOUS"]
         assert self.f.shape[1] == self.n[0] * self.n[1] * self.n[2]
         self.t = float(t)
         self.phase = int(phase)

@@ -1,0 +1,35 @@
+// Host-side launchers of the sweep kernels, one explicit instantiation per precision
+// (kernels_f32.cu, kernels_f64.cu).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mhd {
+
+struct GridDesc;
+struct DevScalars;
+template <typename T> struct FieldSet;
+
+template <typename T>
+struct Launch {
+  // one-time kernel attribute setup (dynamic shared memory opt-in); not capturable
+  static cudaError_t setup();
+  // fluid_axis(dt) with dt read from ds; last: also accumulate c_max of the result
+  static cudaError_t fluid(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
+                           double gamma, double h, DevScalars* ds, int axis, bool last,
+                           bool p64, cudaStream_t s);
+  // CT along axis for both transverse components (t1 then t2)
+  static cudaError_t ct(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
+                        double h, DevScalars* ds, int axis, cudaStream_t s);
+  static cudaError_t cmax(const GridDesc& g, const FieldSet<T>& in, double gamma,
+                          DevScalars* ds, bool p64, cudaStream_t s);
+  static cudaError_t dt(DevScalars* ds, double cfl_h, cudaStream_t s);
+  static cudaError_t sums(long long n, const FieldSet<T>& in, double* partial, int nblocks,
+                          double* out, cudaStream_t s);
+  // dst (T) <- src (dtype 0 float, 1 double), device pointers
+  static cudaError_t from(const void* src, int dtype, T* dst, long long n, cudaStream_t s);
+  // dst (dtype) <- src (T), device pointers
+  static cudaError_t to(const T* src, void* dst, int dtype, long long n, cudaStream_t s);
+};
+
+}  // namespace mhd

@@ -1,0 +1,244 @@
+"""Python binding of the C ABI in include/mhd.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library built from csrc/ for sm_103a; this
+module loads it with ctypes and raises if it is missing: there is no CPU fallback.
+Names follow the C entry points (mhd_create -> Solver(), mhd_step -> Solver.step, ...).
+PyTorch supplies device memory (tensors for device-side upload/download) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+MHD_OK, MHD_ERR_INVALID, MHD_ERR_OOM, MHD_ERR_CUDA, MHD_ERR_UNPHYSICAL, MHD_ERR_TIMEOUT = range(6)
+PERIODIC, OUTFLOW = 0, 1
+FP32, FP64 = 0, 1
+
+# every symbol include/mhd.h declares; tests check the library exports them all
+EXPORTS = ("mhd_create", "mhd_init_fields", "mhd_upload", "mhd_step", "mhd_apply", "mhd_cmax",
+           "mhd_read", "mhd_download", "mhd_sums", "mhd_state", "mhd_set_state", "mhd_sync",
+           "mhd_info", "mhd_stream", "mhd_profile", "mhd_profile_read", "mhd_destroy",
+           "mhd_status_str", "mhd_last_error")
+
+
+class MhdConfig(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
+                ("gamma", C.c_double), ("cfl", C.c_double), ("bc", C.c_int * 3),
+                ("prec", C.c_int), ("fp64_pressure", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class MhdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> C.CDLL:
+    """Load the built library; raises if it was not built (run build.build())."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"CUDA library not built: {p} (run paper_0908_4362_gb300.build.build())")
+    lib = C.CDLL(p)
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+    sig = {
+        "mhd_create": ([C.POINTER(MhdConfig), C.POINTER(vp)], C.c_int),
+        "mhd_init_fields": ([vp, C.POINTER(vp), C.c_double], C.c_int),
+        "mhd_upload": ([vp, C.POINTER(vp), C.c_int, C.c_int, C.c_double], C.c_int),
+        "mhd_step": ([vp, C.c_int, C.c_double, ip, dp], C.c_int),
+        "mhd_apply": ([vp, C.c_int, C.c_int, C.c_double], C.c_int),
+        "mhd_cmax": ([vp, dp], C.c_int),
+        "mhd_read": ([vp, C.POINTER(vp)], C.c_int),
+        "mhd_download": ([vp, C.POINTER(vp), C.c_int, C.c_int], C.c_int),
+        "mhd_sums": ([vp, dp], C.c_int),
+        "mhd_state": ([vp, dp, dp, ip, ip], C.c_int),
+        "mhd_set_state": ([vp, C.c_double, C.c_int, C.c_int], C.c_int),
+        "mhd_sync": ([vp], C.c_int),
+        "mhd_info": ([vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
+        "mhd_stream": ([vp, C.POINTER(vp)], C.c_int),
+        "mhd_profile": ([vp, C.c_int], C.c_int),
+        "mhd_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.c_int], C.c_int),
+        "mhd_destroy": ([vp], None),
+        "mhd_status_str": ([C.c_int], C.c_char_p),
+        "mhd_last_error": ([vp], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptrs8(arrs) -> C.Array:
+    return (C.c_void_p * 8)(*[C.c_void_p(a) for a in arrs])
+
+
+class Solver:
+    """One grid on the GPU (mhd_create ... mhd_destroy)."""
+
+    def __init__(self, n, bc=(PERIODIC,) * 3, h=1.0, gamma=5.0 / 3.0, cfl=0.7, prec=FP32,
+                 fp64_pressure=False, stream=None):
+        self.lib = load_library()
+        cfg = MhdConfig(int(n[0]), int(n[1]), int(n[2]), float(h), float(gamma), float(cfl),
+                        (C.c_int * 3)(*[int(b) for b in bc]), int(prec), int(bool(fp64_pressure)),
+                        C.c_void_p(stream if stream else None))
+        h_ = C.c_void_p()
+        st = self.lib.mhd_create(C.byref(cfg), C.byref(h_))
+        if st != MHD_OK:
+            raise MhdError(st, f"mhd_create: {self.lib.mhd_status_str(st).decode()}")
+        self.ctx = h_
+        self.n = tuple(int(v) for v in n)
+        self.ncells = self.n[0] * self.n[1] * self.n[2]
+        self.prec = prec
+        self.dtype = np.float32 if prec == FP32 else np.float64
+
+    @classmethod
+    def from_problem(cls, prob, prec=FP32, **kw):
+        s = cls(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, prec=prec, **kw)
+        s.init_fields(prob.fields)
+        return s
+
+    def _check(self, st: int, what: str) -> int:
+        if st not in (MHD_OK,):
+            err = self.lib.mhd_last_error(self.ctx).decode()
+            raise MhdError(st, f"{what}: {self.lib.mhd_status_str(st).decode()} {err}".strip())
+        return st
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mhd_destroy(self.ctx)
+            self.ctx = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- state in/out ---------------------------------------------------------------
+    def init_fields(self, fields, t0: float = 0.0, check: bool = True):
+        f = np.ascontiguousarray(np.asarray(fields, dtype=np.float64).reshape(8, -1))
+        assert f.shape[1] == self.ncells
+        st = self.lib.mhd_init_fields(self.ctx, _ptrs8([f[k].ctypes.data for k in range(8)]), t0)
+        return self._check(st, "mhd_init_fields") if check else st
+
+    def upload(self, arrays, t0: float = 0.0, on_device: bool | None = None):
+        """8 arrays (numpy or torch tensors, float32/float64, host or device)."""
+        ptrs, dtype, dev = [], None, on_device
+        for a in arrays:
+            if hasattr(a, "data_ptr"):
+                ptrs.append(a.data_ptr())
+                d = 0 if str(a.dtype) == "torch.float32" else 1
+                dv = a.is_cuda
+            else:
+                ptrs.append(a.ctypes.data)
+                d = 0 if a.dtype == np.float32 else 1
+                dv = False
+            dtype = d if dtype is None else dtype
+            dev = dv if dev is None else dev
+        st = self.lib.mhd_upload(self.ctx, _ptrs8(ptrs), dtype, int(bool(dev)), t0)
+        return self._check(st, "mhd_upload")
+
+    def read(self, check: bool = True) -> np.ndarray:
+        out = np.empty((8, self.ncells), dtype=np.float64)
+        st = self.lib.mhd_read(self.ctx, _ptrs8([out[k].ctypes.data for k in range(8)]))
+        if check:
+            self._check(st, "mhd_read")
+        self.last_status = st
+        return out
+
+    def download(self, arrays, check: bool = True) -> int:
+        ptrs, dtype, dev = [], None, None
+        for a in arrays:
+            if hasattr(a, "data_ptr"):
+                ptrs.append(a.data_ptr())
+                d = 0 if str(a.dtype) == "torch.float32" else 1
+                dv = a.is_cuda
+            else:
+                ptrs.append(a.ctypes.data)
+                d = 0 if a.dtype == np.float32 else 1
+                dv = False
+            dtype = d if dtype is None else dtype
+            dev = dv if dev is None else dev
+        st = self.lib.mhd_download(self.ctx, _ptrs8(ptrs), dtype, int(bool(dev)))
+        return self._check(st, "mhd_download") if check else st
+
+    # --- stepping -------------------------------------------------------------------
+    def step(self, nsteps: int = 1, t_end: float = -1.0, sync: bool = False, check: bool = True):
+        if sync or t_end >= 0:
+            done, t = C.c_int(0), C.c_double(0)
+            st = self.lib.mhd_step(self.ctx, int(nsteps), float(t_end), C.byref(done), C.byref(t))
+            if check:
+                self._check(st, "mhd_step")
+            return done.value
+        st = self.lib.mhd_step(self.ctx, int(nsteps), -1.0, None, None)
+        if check:
+            self._check(st, "mhd_step")
+        return nsteps
+
+    def run_to(self, t_end: float, max_steps: int = 10 ** 7) -> int:
+        return self.step(max_steps, t_end)
+
+    def apply(self, op: int, axis: int, dt: float):
+        return self._check(self.lib.mhd_apply(self.ctx, op, axis, dt), "mhd_apply")
+
+    def cmax(self) -> float:
+        v = C.c_double(0)
+        self._check(self.lib.mhd_cmax(self.ctx, C.byref(v)), "mhd_cmax")
+        return v.value
+
+    def sums(self) -> np.ndarray:
+        out = np.zeros(8)
+        self._check(self.lib.mhd_sums(self.ctx, out.ctypes.data_as(C.POINTER(C.c_double))),
+                    "mhd_sums")
+        return out
+
+    def state(self):
+        t, dtl, stp, ph = C.c_double(), C.c_double(), C.c_int(), C.c_int()
+        self._check(self.lib.mhd_state(self.ctx, C.byref(t), C.byref(dtl), C.byref(stp),
+                                       C.byref(ph)), "mhd_state")
+        return t.value, dtl.value, stp.value, ph.value
+
+    def set_state(self, t: float, step: int, phase: int):
+        return self._check(self.lib.mhd_set_state(self.ctx, t, step, phase), "mhd_set_state")
+
+    def sync(self, check: bool = True) -> int:
+        st = self.lib.mhd_sync(self.ctx)
+        return self._check(st, "mhd_sync") if check else st
+
+    def info(self):
+        n, b = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.mhd_info(self.ctx, C.byref(n), C.byref(b)), "mhd_info")
+        return n.value, b.value
+
+    def profile(self, enable: bool = True):
+        return self._check(self.lib.mhd_profile(self.ctx, int(bool(enable))), "mhd_profile")
+
+    KINDS = ("fluid_x", "fluid_y", "fluid_z", "ct_x", "ct_y", "ct_z", "dt", "other")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        ms = np.zeros(8)
+        cnt = (C.c_longlong * 8)()
+        self._check(self.lib.mhd_profile_read(self.ctx, ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                              cnt, int(bool(reset))), "mhd_profile_read")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KINDS)}
+
+    def stream_handle(self) -> int:
+        s = C.c_void_p()
+        self._check(self.lib.mhd_stream(self.ctx, C.byref(s)), "mhd_stream")
+        return s.value or 0

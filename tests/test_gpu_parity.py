@@ -1,0 +1,206 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element on
+the same seeded inputs.  Tolerances (relative L1 per field, sum|gpu - oracle| / sum|oracle|):
+FP64 <= 1e-12 and FP32 <= 2e-5 after 10 steps; a single sweep operator is held to 1e-13
+(FP64) and 2e-6 (FP32).  Fields that are identically zero in the oracle must stay exactly
+zero on the GPU."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0908_4362_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL, FP32_TOL = 1e-12, 2e-5
+
+
+@pytest.fixture(scope="module")
+def mhd():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_0908_4362_gb300 import build, mhd as m
+    build.build()
+    m.load_library()
+    return m
+
+
+def rel_l1(got, ref):
+    """Per-field relative L1; zero reference fields compare absolutely (must be 0)."""
+    out = np.zeros(8)
+    for k in range(8):
+        den = np.abs(ref[k]).sum()
+        num = np.abs(got[k] - ref[k]).sum()
+        out[k] = num / den if den > 0 else (0.0 if num == 0 else np.inf)
+    return out
+
+
+def run_both(mhd, prob, steps, prec):
+    ref = oracle.Oracle.from_problem(prob)
+    ref.step(steps)
+    with mhd.Solver.from_problem(prob, prec=prec) as s:
+        done = s.step(steps, sync=True)
+        got = s.read()
+        t, _, nst, ph = s.state()
+    assert done == steps and nst == steps and ph == ref.phase
+    assert abs(t - ref.t) <= (1e-13 if prec == mhd.FP64 else 1e-6) * max(1.0, abs(ref.t))
+    return got, ref
+
+
+OP_CASES = [
+    ("periodic_ragged", lambda: I.random_smooth((37, 29, 23), seed=3)),
+    ("mixed_bc", lambda: I.random_smooth((21, 40, 17), seed=4, bc=(1, 0, 1))),
+    ("thin", lambda: I.random_smooth((70, 3, 1), seed=5, bc=(1, 1, 0))),
+]
+
+
+@pytest.mark.parametrize("case", OP_CASES, ids=[c[0] for c in OP_CASES])
+@pytest.mark.parametrize("op", [0, 1], ids=["fluid", "ct"])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_operator(mhd, case, op, axis, prec):
+    prob = case[1]()
+    p = mhd.FP64 if prec == "fp64" else mhd.FP32
+    ref = oracle.Oracle.from_problem(prob)
+    dt = 0.5 * ref.dt()
+    (ref.fluid if op == 0 else ref.ct)(axis, dt)
+    with mhd.Solver.from_problem(prob, prec=p) as s:
+        s.apply(op, axis, dt)
+        got = s.read()
+    err = rel_l1(got, ref.f)
+    tol = 1e-13 if p == mhd.FP64 else 2e-6
+    assert np.all(err <= tol), err
+
+
+STEP_CASES = [
+    ("brio_wu_512", lambda: I.brio_wu(512)),
+    ("brio_wu_y", lambda: I.brio_wu(256, axis=1)),
+    ("orszag_tang_64", lambda: I.orszag_tang(64)),
+    ("orszag_tang_ragged", lambda: I.orszag_tang(45, ny=37)),
+    ("random3d_ragged", lambda: I.random_smooth((19, 23, 17), seed=7)),
+    ("random3d_outflow", lambda: I.random_smooth((33, 18, 26), seed=8, bc=(1, 0, 1))),
+    ("blast_40", lambda: I.blast3d(40)),
+    ("degenerate_z", lambda: I.random_smooth((1, 1, 130), seed=9)),
+    ("single_cell", lambda: I.random_smooth((1, 1, 1), seed=10)),
+    ("batched_instance", lambda: I.batched_instance(3)),
+]
+
+
+@pytest.mark.parametrize("case", STEP_CASES, ids=[c[0] for c in STEP_CASES])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ten_steps(mhd, case, prec):
+    prob = case[1]()
+    p = mhd.FP64 if prec == "fp64" else mhd.FP32
+    steps = 10 if prob.ncells < 2_000_000 else 3
+    got, ref = run_both(mhd, prob, steps, p)
+    err = rel_l1(got, ref.f)
+    assert np.all(err <= (FP64_TOL if p == mhd.FP64 else FP32_TOL)), err
+
+
+def test_brio_wu_to_final_time_fp64(mhd):
+    """Brio-Wu (config: 512 cells, gamma 2, CFL 0.8, outflow) run to t = 0.1 with the last
+    dt clipped: same step count, same final time, same profile."""
+    prob = I.brio_wu(512)
+    ref = oracle.Oracle.from_problem(prob)
+    nref = ref.run_to(0.1)
+    with mhd.Solver.from_problem(prob, prec=mhd.FP64) as s:
+        n = s.run_to(0.1)
+        got = s.read()
+        t, _, _, _ = s.state()
+    assert n == nref and t == 0.1
+    err = rel_l1(got, ref.f)
+    assert np.all(err <= 1e-10), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_smooth_final_time(mhd, prec):
+    """Smooth problems at their final time: the Alfven wave after a full period."""
+    prob = I.alfven_circular(64, axis=2, cfl=0.4)
+    p = mhd.FP64 if prec == "fp64" else mhd.FP32
+    ref = oracle.Oracle.from_problem(prob)
+    nref = ref.run_to(prob.t_end)
+    with mhd.Solver.from_problem(prob, prec=p) as s:
+        n = s.run_to(prob.t_end)
+        got = s.read()
+    assert n == nref
+    err = rel_l1(got, ref.f)
+    assert np.all(err <= (1e-11 if p == mhd.FP64 else 2e-5)), err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cmax_matches(mhd, prec):
+    prob = I.random_smooth((24, 17, 30), seed=12)
+    p = mhd.FP64 if prec == "fp64" else mhd.FP32
+    ref = oracle.Oracle.from_problem(prob).cmax()
+    with mhd.Solver.from_problem(prob, prec=p) as s:
+        got = s.cmax()
+    assert abs(got - ref) <= (1e-14 if p == mhd.FP64 else 2e-6) * ref
+
+
+def test_conservation_and_divb_on_gpu(mhd):
+    prob = I.random_smooth((40, 36, 44), seed=13)
+    with mhd.Solver.from_problem(prob, prec=mhd.FP64) as s:
+        s0 = s.sums()
+        s.step(10, sync=True)
+        s1 = s.sums()
+        f = s.read()
+    scale = np.abs(prob.fields).sum(axis=1)
+    assert np.all(np.abs(s1 - s0) / scale <= 1e-13)
+    ref = oracle.Oracle(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, f)
+    assert ref.divb_max() * prob.h / np.abs(f[5:]).max() <= 1e-13
+
+
+def test_determinism_and_checkpoint(mhd):
+    """Two runs give identical bits, and n steps + checkpoint + restore + n steps equals
+    2n steps."""
+    prob = I.blast3d(32)
+    with mhd.Solver.from_problem(prob, prec=mhd.FP32) as s:
+        s.step(8, sync=True)
+        a = s.read()
+    with mhd.Solver.from_problem(prob, prec=mhd.FP32) as s:
+        s.step(4, sync=True)
+        mid = s.read()
+        t, _, stp, ph = s.state()
+    with mhd.Solver(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, prec=mhd.FP32) as s:
+        s.init_fields(mid)
+        s.set_state(t, stp, ph)
+        s.step(4, sync=True)
+        b = s.read()
+        assert s.state()[2] == 8
+    with mhd.Solver.from_problem(prob, prec=mhd.FP32) as s:
+        s.step(8, sync=True)
+        c = s.read()
+    assert np.array_equal(a, c)
+    assert np.array_equal(a, b)
+
+
+def test_fp64_pressure_flag(mhd):
+    """FP32 sweeps with the pressure recovered in FP64: still within tolerance, and no
+    worse than plain FP32 on a low-beta state."""
+    prob = I.batched_instance(0)
+    ref = oracle.Oracle.from_problem(prob)
+    ref.step(5)
+    errs = []
+    for flag in (False, True):
+        with mhd.Solver(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, prec=mhd.FP32,
+                        fp64_pressure=flag) as s:
+            s.init_fields(prob.fields)
+            s.step(5, sync=True)
+            errs.append(rel_l1(s.read(), ref.f))
+    assert np.all(errs[1] <= FP32_TOL)
+
+
+def test_unphysical_state_reported(mhd):
+    prob = I.random_smooth((8, 8, 8), seed=14)
+    f = prob.fields.copy()
+    f[0, 5] = -1.0
+    s = mhd.Solver(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, prec=mhd.FP64)
+    st = s.init_fields(f, check=False)
+    assert st == mhd.MHD_ERR_UNPHYSICAL
+    s.close()
+
+
+def test_invalid_config_rejected(mhd):
+    with pytest.raises(mhd.MhdError):
+        mhd.Solver((0, 4, 4))
+    with pytest.raises(mhd.MhdError):
+        mhd.Solver((4, 4, 4), cfl=1.5)
