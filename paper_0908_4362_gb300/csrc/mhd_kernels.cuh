@@ -6,8 +6,10 @@
 //
 // Memory layout: 8 separate field arrays (rho, mx, my, mz, E, Bx, By, Bz), flat index
 // (x*ny + y)*nz + z, z contiguous (Sect. 4.1).  B is face centred: Bx[i] on the x-face
-// i-1/2, etc. (Eq. "equat_b").  Every kernel is out of place: it reads the current buffer
-// of a field and writes the other one, so no tile reads what another tile writes.
+// i-1/2, etc. (Eq. "equat_b").  Every sweep kernel is out of place: it reads the current
+// buffer of a field and writes the other one, so no thread reads what another writes.
+// This header holds the per-cell arithmetic shared by the sweep kernels (mhd_march.cuh for
+// x and y sweeps, mhd_segz.cuh for z sweeps) and the auxiliary kernels.
 //
 // Boundaries per axis: periodic (wrap) or outflow (every array index clamped to [0,N-1]).
 #pragma once
@@ -100,36 +102,75 @@ __device__ __forceinline__ T vanleer(T a, T b) {
 template <typename T, bool P64>
 __device__ __forceinline__ int cell_flux(const T u[5], const T b[3], T gamma, T fr[5], T fl[5]) {
   const T rho = u[0];
-  const T vn = Num<T>::div(u[1], rho), vt1 = Num<T>::div(u[2], rho), vt2 = Num<T>::div(u[3], rho);
-  const T b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-  T p;
-  if (P64) {
-    const double rd = (double)rho;
-    const double m1 = u[1], m2 = u[2], m3 = u[3];
-    const double bb0 = b[0], bb1 = b[1], bb2 = b[2];
-    const double ke = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / rd;
-    p = (T)(((double)gamma - 1.0) * ((double)u[4] - ke - 0.5 * (bb0 * bb0 + bb1 * bb1 + bb2 * bb2)));
-  } else {
-    const T v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
-    p = (gamma - T(1)) * (u[4] - T(0.5) * rho * v2 - T(0.5) * b2);
-  }
-  const T ps = p + T(0.5) * b2;
-  const T bv = b[0] * vn + b[1] * vt1 + b[2] * vt2;
-  T F[5];
-  F[0] = u[1];
-  F[1] = u[1] * vn + ps - b[0] * b[0];
-  F[2] = u[2] * vn - b[0] * b[1];
-  F[3] = u[3] * vn - b[0] * b[2];
-  F[4] = (u[4] + ps) * vn - b[0] * bv;
-  const T rad = Num<T>::div(gamma * p, rho) + Num<T>::div(b2, rho);
-  int st = (!(rho > T(0)) || rad < T(0)) ? ST_UNPHYSICAL : 0;
-  const T c = fabs(vn) + Num<T>::sqrt(rad);
+  if constexpr (sizeof(T) == 4) {
+    // FP32: one reciprocal of rho, the radicand as (gamma p + B^2)/rho, and the relaxed
+    // fluxes as c/2 u +- F/2 (the same quantities, fewer instructions)
+    const T ir = T(1) / rho;
+    const T vn = u[1] * ir, vt1 = u[2] * ir, vt2 = u[3] * ir;
+    const T b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    T p;
+    if (P64) {
+      const double m1 = u[1], m2 = u[2], m3 = u[3];
+      const double bb0 = b[0], bb1 = b[1], bb2 = b[2];
+      const double ke = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / (double)rho;
+      p = (T)(((double)gamma - 1.0) * ((double)u[4] - ke - 0.5 * (bb0 * bb0 + bb1 * bb1 + bb2 * bb2)));
+    } else {
+      const T mv = u[1] * vn + u[2] * vt1 + u[3] * vt2;
+      p = (gamma - T(1)) * (u[4] - T(0.5) * mv - T(0.5) * b2);
+    }
+    const T ps = p + T(0.5) * b2;
+    const T bv = b[0] * vn + b[1] * vt1 + b[2] * vt2;
+    T hF[5];
+    hF[0] = T(0.5) * u[1];
+    hF[1] = T(0.5) * (u[1] * vn + ps - b[0] * b[0]);
+    hF[2] = T(0.5) * (u[2] * vn - b[0] * b[1]);
+    hF[3] = T(0.5) * (u[3] * vn - b[0] * b[2]);
+    hF[4] = T(0.5) * ((u[4] + ps) * vn - b[0] * bv);
+    const T rad = (gamma * p + b2) * ir;
+    const int st = (!(rho > T(0)) || rad < T(0)) ? ST_UNPHYSICAL : 0;
+    const T hc = T(0.5) * (fabs(vn) + sqrtf(rad));
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    fr[k] = T(0.5) * (c * u[k] + F[k]);
-    fl[k] = T(0.5) * (c * u[k] - F[k]);
+    for (int k = 0; k < 5; ++k) {
+      fr[k] = hc * u[k] + hF[k];
+      fl[k] = hc * u[k] - hF[k];
+    }
+    return st;
+  } else {
+    // FP64: the oracle's expressions, operation for operation
+    const T vn = Num<T>::div(u[1], rho), vt1 = Num<T>::div(u[2], rho), vt2 = Num<T>::div(u[3], rho);
+    const T b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const T v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+    const T p = (gamma - T(1)) * (u[4] - T(0.5) * rho * v2 - T(0.5) * b2);
+    const T ps = p + T(0.5) * b2;
+    const T bv = b[0] * vn + b[1] * vt1 + b[2] * vt2;
+    T F[5];
+    F[0] = u[1];
+    F[1] = u[1] * vn + ps - b[0] * b[0];
+    F[2] = u[2] * vn - b[0] * b[1];
+    F[3] = u[3] * vn - b[0] * b[2];
+    F[4] = (u[4] + ps) * vn - b[0] * bv;
+    const T rad = Num<T>::div(gamma * p, rho) + Num<T>::div(b2, rho);
+    const int st = (!(rho > T(0)) || rad < T(0)) ? ST_UNPHYSICAL : 0;
+    const T c = fabs(vn) + Num<T>::sqrt(rad);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      fr[k] = T(0.5) * (c * u[k] + F[k]);
+      fl[k] = T(0.5) * (c * u[k] - F[k]);
+    }
+    return st;
   }
-  return st;
+}
+
+// phi(a, b) / 2: the limited correction phi(a/2, b/2) applied to a flux (Eq. "eq:F_n").
+// FP32: ab / (a + b) directly; FP64: the oracle's 2ab/(a+b) halved (the same rounded value).
+template <typename T>
+__device__ __forceinline__ T half_vanleer(T a, T b) {
+  if constexpr (sizeof(T) == 4) {
+    const T ab = a * b;
+    return ab > T(0) ? ab / (a + b) : T(0);
+  } else {
+    return T(0.5) * vanleer(a, b);
+  }
 }
 
 // |v|^2 and |B|^2 summed smallest first, so that c_max does not depend on axis order.
@@ -177,284 +218,6 @@ __device__ __forceinline__ void block_max_to_global(T v, bool nan_seen, DevScala
 
 __host__ __device__ constexpr int axis_t1(int a) { return (a + 1) % 3; }
 __host__ __device__ constexpr int axis_t2(int a) { return (a + 2) % 3; }
-// tile geometry: pencils of S cells along A, W pencils side by side along the "width" axis
-// (z when A != z, for coalescing; y when A == z), one row along the remaining axis.
-__host__ __device__ constexpr int axis_w(int a) { return a == 2 ? 1 : 2; }
-__host__ __device__ constexpr int axis_o(int a) { return a == 0 ? 1 : 0; }
-
-template <typename T> struct FluidTile { static constexpr int S = 64, W = 8, NT = 256; };
-template <> struct FluidTile<double> { static constexpr int S = 32, W = 8, NT = 256; };
-template <typename T> struct CtTile { static constexpr int S = 64, W = 8, NT = 256; };
-template <> struct CtTile<double> { static constexpr int S = 32, W = 8, NT = 256; };
-
-// ------------------------------------------------------------------------------------
-// fluid_A(dt): Algorithm 1.  Stage 1: first-order upwind fluxes of u^t give u^{t+dt/2}
-// (Eq. "eq:Delta_u_half"); stage 2: van Leer limited fluxes of u^{t+dt/2} give u^{t+dt}
-// (Eq. "eq:Delta_u_full").  B is frozen and averaged to cell centres.  LAST: also reduce
-// c_max of the new state for the next step's CFL condition (fused Eq. "equat_CFL").
-// ------------------------------------------------------------------------------------
-template <typename T, int A, bool LAST, bool P64>
-__global__ void __launch_bounds__(FluidTile<T>::NT)
-fluid_kernel(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
-  constexpr int S = FluidTile<T>::S, W = FluidTile<T>::W, NT = FluidTile<T>::NT;
-  constexpr int G = 3, E = S + 2 * G, EW = E * W;
-  constexpr int T1 = axis_t1(A), T2 = axis_t2(A), WX = axis_w(A), OX = axis_o(A);
-  constexpr int DS = (A == 2) ? 1 : W;   // smem stride from cell e to e+1
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);
-  T* sb = su + 5 * EW;
-  T* sfr = sb + 3 * EW;
-  T* sfl = sfr + 5 * EW;
-  T* sh = sfl + 5 * EW;
-
-  const double dtd = ds->dt;
-  const T dth = (T)(dtd / h);
-  const int nA = g.n[A], nW = g.n[WX];
-  const int a0 = blockIdx.x * S, w0 = blockIdx.y * W, io = blockIdx.z;
-  const int bcA = g.bc[A];
-  int st = 0;
-
-  // phase 0: load u and cell-centred B on the extended pencils, stage-1 fluxes
-  for (int idx = threadIdx.x; idx < EW; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / W;
-    const int w = (A == 2) ? idx / E : idx % W;
-    int c[3];
-    c[A] = wrap_index(a0 + e - G, nA, bcA);
-    c[WX] = min(w0 + w, nW - 1);
-    c[OX] = io;
-    const long long gi = c[0] * g.s[0] + c[1] * g.s[1] + c[2] * g.s[2];
-    T u[5], b[3], fr[5], fl[5];
-    u[0] = in.f[0][gi];
-    u[1] = in.f[1 + A][gi];
-    u[2] = in.f[1 + T1][gi];
-    u[3] = in.f[1 + T2][gi];
-    u[4] = in.f[4][gi];
-    const long long gn = gi + (long long)(wrap_index(a0 + e - G + 1, nA, bcA) - c[A]) * g.s[A];
-    const long long g1 = gi + (long long)(wrap_index(c[T1] + 1, g.n[T1], g.bc[T1]) - c[T1]) * g.s[T1];
-    const long long g2 = gi + (long long)(wrap_index(c[T2] + 1, g.n[T2], g.bc[T2]) - c[T2]) * g.s[T2];
-    b[0] = T(0.5) * (in.f[5 + A][gi] + in.f[5 + A][gn]);
-    b[1] = T(0.5) * (in.f[5 + T1][gi] + in.f[5 + T1][g1]);
-    b[2] = T(0.5) * (in.f[5 + T2][gi] + in.f[5 + T2][g2]);
-    st |= cell_flux<T, P64>(u, b, gamma, fr, fl);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      su[k * EW + idx] = u[k];
-      sfr[k * EW + idx] = fr[k];
-      sfl[k * EW + idx] = fl[k];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sb[k * EW + idx] = b[k];
-  }
-  __syncthreads();
-
-  // phase 1: u^{t+dt/2} = u - dt/2h (G1_{e+1/2} - G1_{e-1/2}), G1_{e+1/2} = FR_e - FL_{e+1}
-  const T hd = T(0.5) * dth;
-  for (int idx = threadIdx.x; idx < EW; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / W;
-    if (e < 1 || e >= E - 1) continue;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const T gp = sfr[k * EW + idx] - sfl[k * EW + idx + DS];
-      const T gm = sfr[k * EW + idx - DS] - sfl[k * EW + idx];
-      sh[k * EW + idx] = su[k * EW + idx] - hd * (gp - gm);
-    }
-  }
-  __syncthreads();
-
-  // phase 2: stage-2 fluxes of u^{t+dt/2} (same frozen B), overwriting stage-1 fluxes
-  for (int idx = threadIdx.x; idx < EW; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / W;
-    if (e < 1 || e >= E - 1) continue;
-    T u[5], b[3], fr[5], fl[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) u[k] = sh[k * EW + idx];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) b[k] = sb[k * EW + idx];
-    st |= cell_flux<T, P64>(u, b, gamma, fr, fl);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      sfr[k * EW + idx] = fr[k];
-      sfl[k * EW + idx] = fl[k];
-    }
-  }
-  __syncthreads();
-
-  // phase 3: limited interface fluxes G2_{e+1/2} for e in [G-1, G+S)
-  //   right-moving: FR_e + phi((FR_e - FR_{e-1})/2, (FR_{e+1} - FR_e)/2)    Eq. "eq:F_n"
-  //   left-moving (mirror): FL_{e+1} - phi((FL_{e+1} - FL_e)/2, (FL_{e+2} - FL_{e+1})/2)
-  for (int idx = threadIdx.x; idx < EW; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / W;
-    if (e < G - 1 || e >= G + S) continue;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const T* r = sfr + k * EW + idx;
-      const T* l = sfl + k * EW + idx;
-      const T frm = r[-DS], fr0 = r[0], frp = r[DS];
-      const T fl0 = l[0], fl1 = l[DS], fl2 = l[2 * DS];
-      const T right = fr0 + vanleer(T(0.5) * (fr0 - frm), T(0.5) * (frp - fr0));
-      const T left = fl1 - vanleer(T(0.5) * (fl1 - fl0), T(0.5) * (fl2 - fl1));
-      sh[k * EW + idx] = right - left;
-    }
-  }
-  __syncthreads();
-
-  // phase 4: u^{t+dt} = u^t - dt/h (G2_{e+1/2} - G2_{e-1/2}); store; optional c_max
-  T cm = T(0);
-  bool nan_seen = false;
-  for (int idx = threadIdx.x; idx < EW; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / W;
-    const int w = (A == 2) ? idx / E : idx % W;
-    const int ia = a0 + e - G;
-    if (e < G || e >= G + S || ia >= nA || w0 + w >= nW) continue;
-    int c[3];
-    c[A] = ia;
-    c[WX] = w0 + w;
-    c[OX] = io;
-    const long long gi = c[0] * g.s[0] + c[1] * g.s[1] + c[2] * g.s[2];
-    T un[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-      un[k] = su[k * EW + idx] - dth * (sh[k * EW + idx] - sh[k * EW + idx - DS]);
-    out.f[0][gi] = un[0];
-    out.f[1 + A][gi] = un[1];
-    out.f[1 + T1][gi] = un[2];
-    out.f[1 + T2][gi] = un[3];
-    out.f[4][gi] = un[4];
-    if (!(un[0] > T(0))) st |= ST_UNPHYSICAL;
-    if (LAST) {
-      const T b0 = sb[idx], b1 = sb[EW + idx], b2 = sb[2 * EW + idx];
-      // global component order for the CFL speed is irrelevant: the sums are sorted
-      const T v = cell_cmax<T, P64>(un[0], un[1], un[2], un[3], un[4], b0, b1, b2, gamma, &st);
-      if (v != v) nan_seen = true; else cm = fmax(cm, v);
-    }
-  }
-  if (LAST) block_max_to_global(cm, nan_seen, ds);
-  if (st) atomicOr(&ds->status, st);
-}
-
-// ------------------------------------------------------------------------------------
-// CT_A: for t in (t1, t2): face velocity of the post-fluid state across the t-face,
-// smoothed 1/4(1,2,1) along A (Eq. "eq:averaging_x"), first-order upwind EMF v B_t by the
-// sign of the edge velocity (Eq. "eq:first_flux"), B_t at t+dt/2, limited second-order
-// EMF; then B_t -= dt/h d_A EMF (advection) and B_A += dt/h d_t EMF (constraint), both
-// from the same EMF (Sect. 3; Algorithm 2).
-//
-// Tile: S cells along A; EMF rows (pencils along A) are kept for
-//   group 0: t = WX, rows w0 .. w0+W (W+1 rows) at io,
-//   group 1: t = OX, rows w0 .. w0+W-1 at io,
-//   group 2: t = OX, rows w0 .. w0+W-1 at io+1,
-// which are all the EMFs the tile's B_t and B_A updates need.
-// ------------------------------------------------------------------------------------
-template <typename T, int A>
-__global__ void __launch_bounds__(CtTile<T>::NT)
-ct_kernel(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
-  constexpr int S = CtTile<T>::S, W = CtTile<T>::W, NT = CtTile<T>::NT;
-  constexpr int G = 4, E = S + 2 * G, R = 3 * W + 1, ER = E * R;
-  constexpr int T1 = axis_t1(A), T2 = axis_t2(A), WX = axis_w(A), OX = axis_o(A);
-  constexpr int DS = (A == 2) ? 1 : R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sv = reinterpret_cast<T*>(smem_raw);   // vf, later g = vs B_half
-  T* ss = sv + ER;                           // vs
-  T* sbt = ss + ER;                          // B_t
-  T* se = sbt + ER;                          // E1, later E2
-
-  const T dth = (T)(ds->dt / h);
-  const int nA = g.n[A], nW = g.n[WX], nO = g.n[OX];
-  const int a0 = blockIdx.x * S, w0 = blockIdx.y * W, io = blockIdx.z;
-  const int bcA = g.bc[A];
-  const int io1 = wrap_index(io + 1, nO, g.bc[OX]);
-
-  // phase 0: face velocity across the t-face and B_t on every EMF row
-  for (int idx = threadIdx.x; idx < ER; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / R;
-    const int r = (A == 2) ? idx / E : idx % R;
-    int c[3], cx[3];
-    c[A] = cx[A] = wrap_index(a0 + e - G, nA, bcA);
-    int t;
-    if (r <= W) {                   // group 0: t = WX
-      t = WX;
-      c[WX] = wrap_index(w0 + r, nW, g.bc[WX]);
-      c[OX] = io;
-      cx[WX] = wrap_index(c[WX] - 1, nW, g.bc[WX]);
-      cx[OX] = io;
-    } else {                        // groups 1, 2: t = OX
-      t = OX;
-      const int rr = (r - W - 1) % W, grp = (r - W - 1) / W;
-      c[WX] = cx[WX] = wrap_index(w0 + rr, nW, g.bc[WX]);
-      c[OX] = grp == 0 ? io : io1;
-      cx[OX] = wrap_index(c[OX] - 1, nO, g.bc[OX]);
-    }
-    const long long gi = c[0] * g.s[0] + c[1] * g.s[1] + c[2] * g.s[2];
-    const long long gx = cx[0] * g.s[0] + cx[1] * g.s[1] + cx[2] * g.s[2];
-    sv[idx] = Num<T>::div(in.f[1 + A][gi] + in.f[1 + A][gx], in.f[0][gi] + in.f[0][gx]);
-    sbt[idx] = in.f[5 + t][gi];
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < ER; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / R;
-    if (e < 1 || e >= E - 1) continue;
-    ss[idx] = T(0.25) * (sv[idx + DS] + T(2) * sv[idx] + sv[idx - DS]);
-  }
-  __syncthreads();
-  // first-order upwind EMF at the A-face e+1/2
-  for (int idx = threadIdx.x; idx < ER; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / R;
-    if (e < 1 || e >= E - 2) continue;
-    const T ve = T(0.5) * (ss[idx] + ss[idx + DS]);
-    se[idx] = ve > T(0) ? ss[idx] * sbt[idx] : ss[idx + DS] * sbt[idx + DS];
-  }
-  __syncthreads();
-  // B_t at t + dt/2 and g = vs B_half
-  const T hd = T(0.5) * dth;
-  for (int idx = threadIdx.x; idx < ER; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / R;
-    if (e < 2 || e >= E - 2) continue;
-    const T bh = sbt[idx] - hd * (se[idx] - se[idx - DS]);
-    sv[idx] = ss[idx] * bh;
-  }
-  __syncthreads();
-  // limited second-order EMF at A-faces e+1/2, e in [G-1, G+S-1]
-  for (int idx = threadIdx.x; idx < ER; idx += NT) {
-    const int e = (A == 2) ? idx % E : idx / R;
-    if (e < G - 1 || e > G + S - 1) continue;
-    const T ve = T(0.5) * (ss[idx] + ss[idx + DS]);
-    const T gm = sv[idx - DS], g0 = sv[idx], gp = sv[idx + DS], gpp = sv[idx + 2 * DS];
-    se[idx] = ve > T(0) ? g0 + vanleer(T(0.5) * (g0 - gm), T(0.5) * (gp - g0))
-                        : gp - vanleer(T(0.5) * (gp - g0), T(0.5) * (gpp - gp));
-  }
-  __syncthreads();
-  // outputs: B_t advection for t1, t2 and the constraint on B_A (t1 first, then t2)
-  int st = 0;
-  for (int idx = threadIdx.x; idx < S * W; idx += NT) {
-    const int ei = (A == 2) ? idx % S : idx / W;
-    const int w = (A == 2) ? idx / S : idx % W;
-    const int ia = a0 + ei;
-    if (ia >= nA || w0 + w >= nW) continue;
-    const int e = ei + G;
-    int c[3];
-    c[A] = ia;
-    c[WX] = w0 + w;
-    c[OX] = io;
-    const long long gi = c[0] * g.s[0] + c[1] * g.s[1] + c[2] * g.s[2];
-    auto at = [&](int row, int ee) -> T {
-      return (A == 2) ? se[row * E + ee] : se[ee * R + row];
-    };
-    const int rW0 = w, rW1 = w + 1;              // group 0 rows (t = WX)
-    const int rO0 = W + 1 + w, rO1 = 2 * W + 1 + w;  // groups 1 and 2 (t = OX)
-    const T bw = in.f[5 + WX][gi] - dth * (at(rW0, e) - at(rW0, e - 1));
-    const T bo = in.f[5 + OX][gi] - dth * (at(rO0, e) - at(rO0, e - 1));
-    const T dW = dth * (at(rW1, e - 1) - at(rW0, e - 1));
-    const T dO = dth * (at(rO1, e - 1) - at(rO0, e - 1));
-    T ba = in.f[5 + A][gi];
-    if (T1 == WX) { ba = ba + dW; ba = ba + dO; }
-    else { ba = ba + dO; ba = ba + dW; }
-    out.f[5 + WX][gi] = bw;
-    out.f[5 + OX][gi] = bo;
-    out.f[5 + A][gi] = ba;
-    if (!(bw == bw) || !(bo == bo) || !(ba == ba)) st |= ST_NONFINITE;
-  }
-  if (st) atomicOr(&ds->status, st);
-}
 
 // ------------------------------------------------------------------------------------
 // auxiliary kernels

@@ -3,62 +3,60 @@
 
 #include "mhd_kernels.cuh"
 #include "mhd_launch.h"
+#include "mhd_march.cuh"
+#include "mhd_segz.cuh"
 
 namespace mhd {
 
+// marching sweeps (x, y): S cells per tile along the sweep, NT pencils per block, shared
+// prefetch ring of kMarchRing iterations x NV values per thread
+template <typename T> struct MarchCfg { static constexpr int S = 64, NT = 128; };
 template <typename T>
-static size_t fluid_smem() {
-  constexpr int E = FluidTile<T>::S + 6;
-  return sizeof(T) * 23 * (size_t)E * FluidTile<T>::W;
-}
-template <typename T>
-static size_t ct_smem() {
-  constexpr int E = CtTile<T>::S + 8, R = 3 * CtTile<T>::W + 1;
-  return sizeof(T) * 4 * (size_t)E * R;
-}
+static size_t march_smem(int nv) { return sizeof(T) * (size_t)kMarchRing * nv * MarchCfg<T>::NT; }
+// warp segments (z): warps per block, cells per lane
+constexpr int kSegWarps = 4;
+template <typename T> struct SegK { static constexpr int K = 2; };
 
 template <typename T, int A, bool LAST, bool P64>
-static cudaError_t set_fluid_attr() {
-  return cudaFuncSetAttribute(fluid_kernel<T, A, LAST, P64>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fluid_smem<T>());
+static cudaError_t set_march_attr() {
+  return cudaFuncSetAttribute(fluid_march_xy<T, A, LAST, P64, MarchCfg<T>::S, MarchCfg<T>::NT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem<T>(10));
 }
 template <typename T, int A>
-static cudaError_t set_ct_attr() {
-  return cudaFuncSetAttribute(ct_kernel<T, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)ct_smem<T>());
+static cudaError_t set_ct_march_attr() {
+  return cudaFuncSetAttribute(ct_march_xy<T, A, MarchCfg<T>::S, MarchCfg<T>::NT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem<T>(15));
 }
 
 template <typename T, bool P64>
 static cudaError_t setup_p() {
   cudaError_t e = cudaSuccess;
 #define MHD_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) e = _e; } while (0)
-  MHD_TRY((set_fluid_attr<T, 0, false, P64>()));
-  MHD_TRY((set_fluid_attr<T, 1, false, P64>()));
-  MHD_TRY((set_fluid_attr<T, 2, false, P64>()));
-  MHD_TRY((set_fluid_attr<T, 0, true, P64>()));
-  MHD_TRY((set_fluid_attr<T, 1, true, P64>()));
-  MHD_TRY((set_fluid_attr<T, 2, true, P64>()));
+  MHD_TRY((set_march_attr<T, 0, false, P64>()));
+  MHD_TRY((set_march_attr<T, 1, false, P64>()));
+  MHD_TRY((set_march_attr<T, 0, true, P64>()));
+  MHD_TRY((set_march_attr<T, 1, true, P64>()));
 #undef MHD_TRY
   return e;
-}
-
-template <typename T>
-static dim3 tile_grid(const GridDesc& g, int axis, int S, int W) {
-  const int wa = axis_w(axis), oa = axis_o(axis);
-  return dim3((unsigned)((g.n[axis] + S - 1) / S), (unsigned)((g.n[wa] + W - 1) / W),
-              (unsigned)g.n[oa]);
 }
 
 template <typename T, bool LAST, bool P64>
 static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                            T gamma, double h, DevScalars* ds, int axis, cudaStream_t s) {
-  const dim3 grid = tile_grid<T>(g, axis, FluidTile<T>::S, FluidTile<T>::W);
-  const size_t sm = fluid_smem<T>();
-  switch (axis) {
-    case 0: fluid_kernel<T, 0, LAST, P64><<<grid, FluidTile<T>::NT, sm, s>>>(g, in, out, gamma, h, ds); break;
-    case 1: fluid_kernel<T, 1, LAST, P64><<<grid, FluidTile<T>::NT, sm, s>>>(g, in, out, gamma, h, ds); break;
-    default: fluid_kernel<T, 2, LAST, P64><<<grid, FluidTile<T>::NT, sm, s>>>(g, in, out, gamma, h, ds); break;
+  constexpr int S = MarchCfg<T>::S, NT = MarchCfg<T>::NT;
+  if (axis == 0 || axis == 1) {
+    const int o = axis == 0 ? 1 : 0;
+    const long long np = (long long)g.n[2] * g.n[o];
+    const dim3 grid((unsigned)((np + NT - 1) / NT), (unsigned)((g.n[axis] + S - 1) / S));
+    const size_t sm = march_smem<T>(10);
+    if (axis == 0) fluid_march_xy<T, 0, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+    else fluid_march_xy<T, 1, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+    return;
   }
+  constexpr int K = SegK<T>::K, SEG = 32 * K - 6;
+  const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
+  fluid_seg_z<T, LAST, P64, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
+                                            32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
 }
 
 template <typename T>
@@ -79,14 +77,23 @@ static cudaError_t fluid_impl(const GridDesc& g, const FieldSet<T>& in, const Fi
 template <typename T>
 static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                            double h, DevScalars* ds, int axis, cudaStream_t s) {
-  const dim3 grid = tile_grid<T>(g, axis, CtTile<T>::S, CtTile<T>::W);
-  const size_t sm = ct_smem<T>();
-  switch (axis) {
-    case 0: ct_kernel<T, 0><<<grid, CtTile<T>::NT, sm, s>>>(g, in, out, h, ds); break;
-    case 1: ct_kernel<T, 1><<<grid, CtTile<T>::NT, sm, s>>>(g, in, out, h, ds); break;
-    default: ct_kernel<T, 2><<<grid, CtTile<T>::NT, sm, s>>>(g, in, out, h, ds); break;
+  constexpr int S = MarchCfg<T>::S, NT = MarchCfg<T>::NT;
+  if (axis == 0 || axis == 1) {
+    const int o = axis == 0 ? 1 : 0;
+    const long long np = (long long)g.n[2] * g.n[o];
+    const dim3 grid((unsigned)((np + NT - 1) / NT), (unsigned)((g.n[axis] + S - 1) / S));
+    const size_t sm = march_smem<T>(15);
+    if (axis == 0) ct_march_xy<T, 0, S, NT><<<grid, NT, sm, s>>>(g, in, out, h, ds);
+    else ct_march_xy<T, 1, S, NT><<<grid, NT, sm, s>>>(g, in, out, h, ds);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  {
+    constexpr int K = SegK<T>::K, SEG = 32 * K - 8;
+    const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
+    ct_seg_z<T, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps), 32 * kSegWarps, 0,
+                                s>>>(g, in, out, h, ds);
+    return cudaGetLastError();
+  }
 }
 
 template <typename T>
@@ -113,9 +120,8 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
   template <> cudaError_t Launch<T>::setup() {                                              \
     cudaError_t e = setup_p<T, false>();                                                    \
     if (sizeof(T) == 4) { cudaError_t e2 = setup_p<T, true>(); if (e2 != cudaSuccess) e = e2; } \
-    cudaError_t e3 = set_ct_attr<T, 0>(); if (e3 != cudaSuccess) e = e3;                    \
-    e3 = set_ct_attr<T, 1>(); if (e3 != cudaSuccess) e = e3;                                \
-    e3 = set_ct_attr<T, 2>(); if (e3 != cudaSuccess) e = e3;                                \
+    cudaError_t e3 = set_ct_march_attr<T, 0>(); if (e3 != cudaSuccess) e = e3;              \
+    e3 = set_ct_march_attr<T, 1>(); if (e3 != cudaSuccess) e = e3;                          \
     return e;                                                                               \
   }                                                                                         \
   template <> cudaError_t Launch<T>::fluid(const GridDesc& g, const FieldSet<T>& in,        \

@@ -1,0 +1,424 @@
+// Marching fluid sweep: one thread per pencil, walking along the sweep axis with a sliding
+// register window (Algorithm 1 evaluated cell by cell as the pencil streams in).
+//
+// At iteration k the thread has loaded cell j = js + k and holds, in registers,
+//   u(j-1..j-3), cell-centred B (j-1..j-3), the stage-1 right-moving flux of j-1, the
+//   first-order interface flux at (j-2)+1/2, the stage-2 fluxes and their differences
+//   around j-3, and the limited interface flux at (j-4)+1/2.
+// It then forms the stage-1 fluxes of j, the first-order flux at (j-1)+1/2, the half step
+// u^{t+dt/2}(j-1) (Eq. "eq:Delta_u_half"), its stage-2 fluxes, the limited interface flux at
+// (j-3)+1/2 (Eqs. "eq:Delta_F", "eq:limiter", "eq:F_n" and the mirrored left-moving form)
+// and the full update of cell j-3 (Eq. "eq:Delta_u_full").  Every flux is evaluated once.
+//
+// The operation order of each expression matches the oracle (phi(a/2, b/2) is evaluated
+// as phi(a, b)/2, which is the same rounded value), so the FP64 build without FMA
+// contraction reproduces it bit for bit.
+#pragma once
+
+#include "mhd_kernels.cuh"
+
+namespace mhd {
+
+template <typename T, bool P64, bool LAST>
+struct FluidPencil {
+  T u1[5], u2[5], u3[5];   // u(j-1), u(j-2), u(j-3)
+  T b1[3], b2[3], b3[3];   // cell-centred B at j-1, j-2, j-3
+  T fr1[5];                // stage-1 FR(j-1)
+  T g1[5];                 // first-order interface flux at (j-2)+1/2
+  T frA[5], frB[5];        // stage-2 FR(j-3), FR(j-2)
+  T dRp[5];                // FR2(j-3) - FR2(j-4)
+  T flL[5], dLp[5];        // FL2(j-2), FL2(j-2) - FL2(j-3)
+  T g2[5];                 // limited interface flux at (j-4)+1/2
+  int st;
+
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      u1[c] = u2[c] = u3[c] = T(0);
+      fr1[c] = g1[c] = frA[c] = frB[c] = dRp[c] = flL[c] = dLp[c] = g2[c] = T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b1[c] = b2[c] = b3[c] = T(0);
+    st = 0;
+  }
+
+  // Push cell j (iteration k).  Returns true when `out` holds u^{t+dt} of cell j-3, and
+  // then `bout` its cell-centred B (for the fused CFL speed).
+  __device__ __forceinline__ bool push(int k, const T u0[5], const T b0[3], T gamma, T dth,
+                                       T hd, T out[5], T bout[3]) {
+    T fr0[5], fl0[5];
+    st |= cell_flux<T, P64>(u0, b0, gamma, fr0, fl0);
+    T uh[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const T g1c = fr1[c] - fl0[c];                 // first-order flux at (j-1)+1/2
+      uh[c] = u1[c] - hd * (g1c - g1[c]);            // u^{t+dt/2}(j-1)
+      g1[c] = g1c;
+      fr1[c] = fr0[c];
+    }
+    T fr2[5], fl2[5];
+    const int s2 = cell_flux<T, P64>(uh, b1, gamma, fr2, fl2);
+    if (k >= 2) st |= s2;
+    T g2c[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const T dRc = frB[c] - frA[c];                 // FR2(j-2) - FR2(j-3)
+      const T right = frA[c] + half_vanleer(dRp[c], dRc);
+      const T dLc = fl2[c] - flL[c];                 // FL2(j-1) - FL2(j-2)
+      const T left = flL[c] - half_vanleer(dLp[c], dLc);
+      g2c[c] = right - left;                         // limited flux at (j-3)+1/2
+      dRp[c] = dRc;
+      frA[c] = frB[c];
+      frB[c] = fr2[c];
+      dLp[c] = dLc;
+      flL[c] = fl2[c];
+    }
+    const bool valid = k >= 6;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      out[c] = u3[c] - dth * (g2c[c] - g2[c]);
+      g2[c] = g2c[c];
+      u3[c] = u2[c];
+      u2[c] = u1[c];
+      u1[c] = u0[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      bout[c] = b3[c];
+      if (LAST) {
+        b3[c] = b2[c];
+        b2[c] = b1[c];
+      }
+      b1[c] = b0[c];
+    }
+    if (!LAST) {
+      // b3 only feeds the CFL speed of the LAST variant
+    }
+    return valid;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ long long wrap_off(int i, int n, int bc, long long stride) {
+  return (long long)wrap_index(i, n, bc) * stride;
+}
+
+// Asynchronous global -> shared copies (cp.async): each thread prefetches the inputs of
+// the iterations D ahead of the one it computes into its own slots of a shared ring, so
+// that the loads of a march stay in flight while the arithmetic of earlier cells runs.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// prefetch depth (iterations ahead) and ring length of the marching kernels
+constexpr int kMarchDepth = 4;
+constexpr int kMarchRing = kMarchDepth + 1;
+
+// ------------------------------------------------------------------------------------
+// x or y sweep (A = 0, 1): threads take consecutive positions of the transverse plane with
+// z fastest (coalesced rows per field); each thread marches its pencil over S cells plus
+// the 6-cell halo.  blockIdx.y selects the tile along the sweep.
+// ------------------------------------------------------------------------------------
+template <typename T, int A, bool LAST, bool P64, int S, int NT>
+__global__ void __launch_bounds__(NT)
+fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
+  static_assert(A == 0 || A == 1, "x or y sweep");
+  constexpr int O = (A == 0) ? 1 : 0;       // the transverse axis that is not z
+  constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
+  const long long p = (long long)blockIdx.x * NT + threadIdx.x;
+  const int z = (int)(p % g.n[2]);
+  const long long o_ = p / g.n[2];
+  const int o = (int)(o_ < g.n[O] ? o_ : g.n[O]);
+  const int a0 = blockIdx.y * S;
+  const int nA = g.n[A], bcA = g.bc[A];
+  const bool active = o_ < g.n[O];
+  const T dth = (T)(ds->dt / h);
+  const T hd = T(0.5) * dth;
+  const int zc = min(z, g.n[2] - 1), oc = min(o, g.n[O] - 1);
+  const long long base = (long long)zc + (long long)oc * g.s[O];
+  // offsets of the +1 neighbour across the t1 and t2 faces (for the cell-centred B)
+  const long long s1 = (T1 == 2) ? (long long)(wrap_index(zc + 1, g.n[2], g.bc[2]) - zc)
+                                 : (long long)(wrap_index(oc + 1, g.n[O], g.bc[O]) - oc) * g.s[O];
+  const long long s2 = (T2 == 2) ? (long long)(wrap_index(zc + 1, g.n[2], g.bc[2]) - zc)
+                                 : (long long)(wrap_index(oc + 1, g.n[O], g.bc[O]) - oc) * g.s[O];
+  const T* __restrict__ pr = in.f[0];
+  const T* __restrict__ pn = in.f[1 + A];
+  const T* __restrict__ p1 = in.f[1 + T1];
+  const T* __restrict__ p2 = in.f[1 + T2];
+  const T* __restrict__ pe = in.f[4];
+  const T* __restrict__ bn = in.f[5 + A];
+  const T* __restrict__ bt1 = in.f[5 + T1];
+  const T* __restrict__ bt2 = in.f[5 + T2];
+  const long long sA = g.s[A];
+
+  FluidPencil<T, P64, LAST> P;
+  P.init();
+  const int js = a0 - 3;
+  const int kend = min(S, nA - a0) + 6;       // iterations needed for this tile
+  // shared ring: [slot][value][thread], 10 values per iteration (u, B_n(j+1), B_t1 x2, B_t2 x2)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  constexpr int NV = 10;
+  auto issue = [&](int kk) {
+    if (kk < kend) {
+      const int j = js + kk;
+      const long long c = base + wrap_off<T>(j, nA, bcA, sA);
+      const long long cn = base + wrap_off<T>(j + 1, nA, bcA, sA);
+      T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
+      cp_async_elem(slot + 0 * NT, pr + c);
+      cp_async_elem(slot + 1 * NT, pn + c);
+      cp_async_elem(slot + 2 * NT, p1 + c);
+      cp_async_elem(slot + 3 * NT, p2 + c);
+      cp_async_elem(slot + 4 * NT, pe + c);
+      cp_async_elem(slot + 5 * NT, bn + cn);
+      cp_async_elem(slot + 6 * NT, bt1 + c);
+      cp_async_elem(slot + 7 * NT, bt1 + c + s1);
+      cp_async_elem(slot + 8 * NT, bt2 + c);
+      cp_async_elem(slot + 9 * NT, bt2 + c + s2);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kMarchDepth; ++d) issue(d);
+  // B_n of the first cell (each iteration brings B_n one cell ahead)
+  T bn_cur = bn[base + wrap_off<T>(js, nA, bcA, sA)];
+  T cm = T(0);
+  bool nan_seen = false;
+  for (int k = 0; k < kend; ++k) {
+    issue(k + kMarchDepth);
+    cp_async_wait<kMarchDepth>();
+    const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+    const int j = js + k;
+    T u0[5], b0[3];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u0[c] = slot[c * NT];
+    const T bn_next = slot[5 * NT];
+    b0[0] = T(0.5) * (bn_cur + bn_next);
+    b0[1] = T(0.5) * (slot[6 * NT] + slot[7 * NT]);
+    b0[2] = T(0.5) * (slot[8 * NT] + slot[9 * NT]);
+    bn_cur = bn_next;
+    T un[5], bo[3];
+    if (P.push(k, u0, b0, gamma, dth, hd, un, bo)) {
+      const int ia = j - 3;
+      if (active) {
+        const long long co = base + (long long)ia * sA;
+        out.f[0][co] = un[0];
+        out.f[1 + A][co] = un[1];
+        out.f[1 + T1][co] = un[2];
+        out.f[1 + T2][co] = un[3];
+        out.f[4][co] = un[4];
+        if (!(un[0] > T(0))) P.st |= ST_UNPHYSICAL;
+        if (LAST) {
+          const T v = cell_cmax<T, P64>(un[0], un[1], un[2], un[3], un[4], bo[0], bo[1], bo[2],
+                                        gamma, &P.st);
+          if (v != v) nan_seen = true; else cm = fmax(cm, v);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (LAST) block_max_to_global(cm, nan_seen, ds);
+  if (active && P.st) atomicOr(&ds->status, P.st);
+}
+
+}  // namespace mhd
+
+namespace mhd {
+
+// ------------------------------------------------------------------------------------
+// Marching constrained transport (Algorithm 2; Eqs. "eq:averaging_x", "eq:first_flux").
+// One EMF pipeline follows one pencil of a transverse face component B_t along the sweep.
+// Pushing cell j (face velocity vf(j) across the t-face and B_t(j)) yields, 4 cells
+// behind, the advected B_t(j-4) and the limited EMF at the A-face (j-4)+1/2; the EMF at
+// (j-5)+1/2 (the previous one) is what the constraint on B_A(j-4) uses.
+// Operation order matches the oracle expression by expression.
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct EmfPipe {
+  T vf1, vf2;          // vf(j-1), vf(j-2)
+  T vs1, vs2, vs3;     // vs(j-2), vs(j-3), vs(j-4)
+  T b1, b2, b3, b4;    // B_t(j-1), B_t(j-2), B_t(j-3), B_t(j-4)
+  T e1p;               // first-order EMF at (j-3)+1/2
+  T g3, g4;            // g(j-3), g(j-4)  (g = vs * B_t at t + dt/2)
+  T dp;                // g(j-3) - g(j-4)
+  T pp;                // phi(g(j-4) - g(j-5), g(j-3) - g(j-4)) / 2
+  T e2p;               // limited EMF at (j-5)+1/2
+
+  __device__ __forceinline__ void init() {
+    vf1 = vf2 = vs1 = vs2 = vs3 = b1 = b2 = b3 = b4 = e1p = g3 = g4 = dp = pp = e2p = T(0);
+  }
+
+  // returns the advected B_t(j-4); e2_prev receives the EMF at (j-5)+1/2
+  __device__ __forceinline__ T push(T vf0, T b0, T dth, T hd, T* e2_prev) {
+    const T vs0 = T(0.25) * (vf0 + T(2) * vf1 + vf2);           // vs(j-1)
+    const T ve1 = T(0.5) * (vs1 + vs0);                           // edge velocity (j-2)+1/2
+    const T e1 = ve1 > T(0) ? vs1 * b2 : vs0 * b1;               // first-order EMF (j-2)+1/2
+    const T bh = b2 - hd * (e1 - e1p);                            // B_t(j-2) at t + dt/2
+    const T g2 = vs1 * bh;                                        // g(j-2)
+    const T dn = g2 - g3;                                         // g(j-2) - g(j-3)
+    const T pn = half_vanleer(dp, dn);                            // phi/2 at (j-3)
+    const T ve4 = T(0.5) * (vs3 + vs2);                           // edge velocity (j-4)+1/2
+    const T e2 = ve4 > T(0) ? g4 + pp : g3 - pn;
+    const T bt = b4 - dth * (e2 - e2p);                           // advected B_t(j-4)
+    *e2_prev = e2p;
+    // shift
+    vf2 = vf1; vf1 = vf0;
+    vs3 = vs2; vs2 = vs1; vs1 = vs0;
+    b4 = b3; b3 = b2; b2 = b1; b1 = b0;
+    e1p = e1;
+    g4 = g3; g3 = g2;
+    dp = dn;
+    pp = pn;
+    e2p = e2;
+    return bt;
+  }
+};
+
+// Offsets of the four cells a thread needs across one transverse axis t: the row itself
+// (own), its lower neighbour (the across-face cell of its EMF row), its upper neighbour
+// (the row whose EMF enters the constraint) and that row's across-face cell, which is
+// always either the own cell or the lower neighbour (wrap or clamp).
+struct TransverseOffsets {
+  long long lo, hi;      // offsets of the lower and upper neighbour rows
+  bool hi_across_lo;     // the upper row's across-face cell is the lower neighbour
+};
+
+__device__ __forceinline__ TransverseOffsets transverse_offsets(int c, int n, int bc,
+                                                               long long stride) {
+  TransverseOffsets t;
+  const int lo = wrap_index(c - 1, n, bc), hi = wrap_index(c + 1, n, bc);
+  const int hi_across = wrap_index(hi - 1, n, bc);
+  t.lo = (long long)(lo - c) * stride;
+  t.hi = (long long)(hi - c) * stride;
+  t.hi_across_lo = (hi_across != c);
+  return t;
+}
+
+template <typename T>
+struct CtColumn {
+  EmfPipe<T> own1, nb1, own2, nb2;
+  T ba1, ba2, ba3, ba4;   // B_A(j-1..j-4)
+
+  __device__ __forceinline__ void init() {
+    own1.init(); nb1.init(); own2.init(); nb2.init();
+    ba1 = ba2 = ba3 = ba4 = T(0);
+  }
+
+  // r[5], m[5]: rho and m_A at (own, lo1, hi1, lo2, hi2); b1o/b1h: B_t1 at own/hi1 row,
+  // b2o/b2h: B_t2 at own/hi2 row; ba: B_A(j).  Outputs for cell j-4.
+  __device__ __forceinline__ void push(const T r[5], const T m[5], T b1o, T b1h, T b2o, T b2h,
+                                       T ba, bool hx1, bool hx2, T dth, T hd, T* bt1, T* bt2,
+                                       T* bA) {
+    const T vo1 = Num<T>::div(m[0] + m[1], r[0] + r[1]);
+    const T vn1 = hx1 ? Num<T>::div(m[2] + m[1], r[2] + r[1]) : Num<T>::div(m[2] + m[0], r[2] + r[0]);
+    const T vo2 = Num<T>::div(m[0] + m[3], r[0] + r[3]);
+    const T vn2 = hx2 ? Num<T>::div(m[4] + m[3], r[4] + r[3]) : Num<T>::div(m[4] + m[0], r[4] + r[0]);
+    T eo1, en1, eo2, en2;
+    *bt1 = own1.push(vo1, b1o, dth, hd, &eo1);
+    nb1.push(vn1, b1h, dth, hd, &en1);
+    *bt2 = own2.push(vo2, b2o, dth, hd, &eo2);
+    nb2.push(vn2, b2h, dth, hd, &en2);
+    T b = ba4 + dth * (en1 - eo1);           // constraint from t1, then t2
+    b = b + dth * (en2 - eo2);
+    *bA = b;
+    ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = ba;
+  }
+};
+
+// x or y sweep of the constrained transport; thread layout as fluid_march_xy
+template <typename T, int A, int S, int NT>
+__global__ void __launch_bounds__(NT)
+ct_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
+  static_assert(A == 0 || A == 1, "x or y sweep");
+  constexpr int O = (A == 0) ? 1 : 0;
+  constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
+  const long long p = (long long)blockIdx.x * NT + threadIdx.x;
+  const int z = (int)(p % g.n[2]);
+  const long long o_ = p / g.n[2];
+  const int oc = (int)(o_ < g.n[O] ? o_ : g.n[O] - 1);
+  const int a0 = blockIdx.y * S;
+  const int nA = g.n[A], bcA = g.bc[A];
+  const bool active = o_ < g.n[O];
+  const T dth = (T)(ds->dt / h);
+  const T hd = T(0.5) * dth;
+  const long long base = (long long)z + (long long)oc * g.s[O];
+  const int c1 = (T1 == 2) ? z : oc, c2 = (T2 == 2) ? z : oc;
+  const TransverseOffsets o1 = transverse_offsets(c1, g.n[T1], g.bc[T1], g.s[T1]);
+  const TransverseOffsets o2 = transverse_offsets(c2, g.n[T2], g.bc[T2], g.s[T2]);
+  const T* __restrict__ pr = in.f[0];
+  const T* __restrict__ pm = in.f[1 + A];
+  const T* __restrict__ pb1 = in.f[5 + T1];
+  const T* __restrict__ pb2 = in.f[5 + T2];
+  const T* __restrict__ pba = in.f[5 + A];
+  const long long sA = g.s[A];
+  CtColumn<T> col;
+  col.init();
+  const int js = a0 - 4;
+  const int kend = min(S, nA - a0) + 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  constexpr int NV = 15;
+  auto issue = [&](int kk) {
+    if (kk < kend) {
+      const long long c = base + (long long)wrap_index(js + kk, nA, bcA) * sA;
+      T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
+      cp_async_elem(slot + 0 * NT, pr + c);
+      cp_async_elem(slot + 1 * NT, pr + c + o1.lo);
+      cp_async_elem(slot + 2 * NT, pr + c + o1.hi);
+      cp_async_elem(slot + 3 * NT, pr + c + o2.lo);
+      cp_async_elem(slot + 4 * NT, pr + c + o2.hi);
+      cp_async_elem(slot + 5 * NT, pm + c);
+      cp_async_elem(slot + 6 * NT, pm + c + o1.lo);
+      cp_async_elem(slot + 7 * NT, pm + c + o1.hi);
+      cp_async_elem(slot + 8 * NT, pm + c + o2.lo);
+      cp_async_elem(slot + 9 * NT, pm + c + o2.hi);
+      cp_async_elem(slot + 10 * NT, pb1 + c);
+      cp_async_elem(slot + 11 * NT, pb1 + c + o1.hi);
+      cp_async_elem(slot + 12 * NT, pb2 + c);
+      cp_async_elem(slot + 13 * NT, pb2 + c + o2.hi);
+      cp_async_elem(slot + 14 * NT, pba + c);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kMarchDepth; ++d) issue(d);
+  int st = 0;
+  for (int k = 0; k < kend; ++k) {
+    issue(k + kMarchDepth);
+    cp_async_wait<kMarchDepth>();
+    const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+    const int j = js + k;
+    T r[5], m[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      r[q] = slot[q * NT];
+      m[q] = slot[(5 + q) * NT];
+    }
+    T bt1, bt2, bA;
+    col.push(r, m, slot[10 * NT], slot[11 * NT], slot[12 * NT], slot[13 * NT], slot[14 * NT],
+             o1.hi_across_lo, o2.hi_across_lo, dth, hd, &bt1, &bt2, &bA);
+    if (k >= 8 && active) {
+      const long long co = base + (long long)(j - 4) * sA;
+      out.f[5 + T1][co] = bt1;
+      out.f[5 + T2][co] = bt2;
+      out.f[5 + A][co] = bA;
+      if (!(bt1 == bt1) || !(bt2 == bt2) || !(bA == bA)) st |= ST_NONFINITE;
+    }
+  }
+  cp_async_wait<0>();
+  if (active && st) atomicOr(&ds->status, st);
+}
+
+}  // namespace mhd

@@ -1,0 +1,258 @@
+// z sweeps as warp-cooperative segments.  The z pencil is the contiguous axis, so the 32
+// lanes of a warp hold 32 K consecutive cells of one pencil (lane l: cells lK .. lK+K-1):
+// loads coalesce along z, neighbours inside a lane are registers, and the one neighbour
+// per shift that lives in the next or previous lane comes from a warp shuffle.  Each warp
+// updates the cells whose full stencil lies inside its window: 32K - 6 for the fluid sweep
+// (halo 3 per side), 32K - 8 for the constrained transport (halo 4).
+// Per-cell arithmetic and its order are the oracle's (Algorithms 1 and 2).
+#pragma once
+
+#include "mhd_kernels.cuh"
+#include "mhd_march.cuh"
+
+namespace mhd {
+
+template <typename T>
+__device__ __forceinline__ T shdown(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+template <typename T>
+__device__ __forceinline__ T shup(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
+// value of the next cell (to the right along z) for each of the lane's K cells
+template <typename T, int K>
+__device__ __forceinline__ void next_cell(const T (&x)[K], T (&xn)[K]) {
+  const T from_next_lane = shdown(x[0]);
+#pragma unroll
+  for (int i = 0; i < K; ++i) xn[i] = (i + 1 < K) ? x[i + 1] : from_next_lane;
+}
+// value of the previous cell for each of the lane's K cells
+template <typename T, int K>
+__device__ __forceinline__ void prev_cell(const T (&x)[K], T (&xp)[K]) {
+  const T from_prev_lane = shup(x[K - 1]);
+#pragma unroll
+  for (int i = 0; i < K; ++i) xp[i] = (i > 0) ? x[i - 1] : from_prev_lane;
+}
+
+template <typename T, bool LAST, bool P64, int NW, int K>
+__global__ void __launch_bounds__(32 * NW)
+fluid_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
+  constexpr int H = 3, SEG = 32 * K - 2 * H;
+  const int lane = threadIdx.x & 31;
+  const long long wid = (long long)blockIdx.x * NW + (threadIdx.x >> 5);
+  const int nz = g.n[2], bcz = g.bc[2];
+  const int nseg = (nz + SEG - 1) / SEG;
+  const long long pencil = wid / nseg;
+  const int s0 = (int)(wid % nseg) * SEG;
+  const long long npen = (long long)g.n[0] * g.n[1];
+  const bool warp_active = pencil < npen;
+  const long long pc = warp_active ? pencil : npen - 1;
+  const int x = (int)(pc / g.n[1]), y = (int)(pc % g.n[1]);
+  const T dth = (T)(ds->dt / h);
+  const T hd = T(0.5) * dth;
+  const long long row = (long long)x * g.s[0] + (long long)y * g.s[1];
+  const long long r1 = row + (long long)(wrap_index(x + 1, g.n[0], g.bc[0]) - x) * g.s[0];
+  const long long r2 = row + (long long)(wrap_index(y + 1, g.n[1], g.bc[1]) - y) * g.s[1];
+  const int z0 = s0 - H + lane * K;     // the lane's first cell
+  // local coordinates of a z sweep: n = z, t1 = x, t2 = y
+  T u[K][5], b[K][3];
+  int st = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int zc = wrap_index(z0 + i, nz, bcz), zn = wrap_index(z0 + i + 1, nz, bcz);
+    u[i][0] = __ldg(in.f[0] + row + zc);
+    u[i][1] = __ldg(in.f[3] + row + zc);
+    u[i][2] = __ldg(in.f[1] + row + zc);
+    u[i][3] = __ldg(in.f[2] + row + zc);
+    u[i][4] = __ldg(in.f[4] + row + zc);
+    b[i][0] = T(0.5) * (__ldg(in.f[7] + row + zc) + __ldg(in.f[7] + row + zn));
+    b[i][1] = T(0.5) * (__ldg(in.f[5] + row + zc) + __ldg(in.f[5] + r1 + zc));
+    b[i][2] = T(0.5) * (__ldg(in.f[6] + row + zc) + __ldg(in.f[6] + r2 + zc));
+  }
+  // stage 1: first-order fluxes, half step
+  T uh[K][5];
+  {
+    T fr[5][K], fl[5][K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      T a[5], c[5];
+      st |= cell_flux<T, P64>(u[i], b[i], gamma, a, c);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) { fr[q][i] = a[q]; fl[q][i] = c[q]; }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      T fln[K], g1[K], g1p[K];
+      next_cell<T, K>(fl[q], fln);
+#pragma unroll
+      for (int i = 0; i < K; ++i) g1[i] = fr[q][i] - fln[i];       // first-order flux at +1/2
+      prev_cell<T, K>(g1, g1p);
+#pragma unroll
+      for (int i = 0; i < K; ++i) uh[i][q] = u[i][q] - hd * (g1[i] - g1p[i]);
+    }
+  }
+  // stage 2: limited fluxes of u^{t+dt/2}, full update
+  T un[K][5];
+  {
+    T fr2[5][K], fl2[5][K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      T a[5], c[5];
+      const int s2 = cell_flux<T, P64>(uh[i], b[i], gamma, a, c);
+      const int w = lane * K + i;                          // window cell, 1 .. 32K-2 valid
+      if (w >= 1 && w <= 32 * K - 2) st |= s2;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) { fr2[q][i] = a[q]; fl2[q][i] = c[q]; }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      T frn[K], dR[K], dRp[K], fln[K], dL[K], dLn[K], g2[K], g2p[K];
+      next_cell<T, K>(fr2[q], frn);
+#pragma unroll
+      for (int i = 0; i < K; ++i) dR[i] = frn[i] - fr2[q][i];      // FR2(w+1) - FR2(w)
+      prev_cell<T, K>(dR, dRp);
+      next_cell<T, K>(fl2[q], fln);
+#pragma unroll
+      for (int i = 0; i < K; ++i) dL[i] = fln[i] - fl2[q][i];      // FL2(w+1) - FL2(w)
+      next_cell<T, K>(dL, dLn);
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const T right = fr2[q][i] + half_vanleer(dRp[i], dR[i]);
+        const T left = fln[i] - half_vanleer(dL[i], dLn[i]);
+        g2[i] = right - left;                                      // limited flux at +1/2
+      }
+      prev_cell<T, K>(g2, g2p);
+#pragma unroll
+      for (int i = 0; i < K; ++i) un[i][q] = u[i][q] - dth * (g2[i] - g2p[i]);
+    }
+  }
+  T cm = T(0);
+  bool nan_seen = false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int w = lane * K + i, z = z0 + i;
+    if (warp_active && w >= H && w < H + SEG && z < nz) {
+      const long long co = row + z;
+      out.f[0][co] = un[i][0];
+      out.f[3][co] = un[i][1];
+      out.f[1][co] = un[i][2];
+      out.f[2][co] = un[i][3];
+      out.f[4][co] = un[i][4];
+      if (!(un[i][0] > T(0))) st |= ST_UNPHYSICAL;
+      if (LAST) {
+        const T v = cell_cmax<T, P64>(un[i][0], un[i][1], un[i][2], un[i][3], un[i][4], b[i][0],
+                                      b[i][1], b[i][2], gamma, &st);
+        if (v != v) nan_seen = true; else cm = fmax(cm, v);
+      }
+    }
+  }
+  if (LAST) block_max_to_global(cm, nan_seen, ds);
+  if (warp_active && st) atomicOr(&ds->status, st);
+}
+
+// one EMF pipeline over the window: bt[] becomes the advected B_t (valid on window cells
+// 4 .. 32K-5) and e2m[] the limited EMF at each cell's lower face (4 .. 32K-4)
+template <typename T, int K>
+__device__ __forceinline__ void emf_seg(const T (&vf)[K], T (&bt)[K], T dth, T hd, T (&e2m)[K]) {
+  T vn[K], vp[K], vs[K], vsn[K], f[K], fn[K], e1[K], e1p[K], gg[K], ggn[K], d[K], dp[K], P[K], Pn[K];
+  next_cell<T, K>(vf, vn);
+  prev_cell<T, K>(vf, vp);
+#pragma unroll
+  for (int i = 0; i < K; ++i) vs[i] = T(0.25) * (vn[i] + T(2) * vf[i] + vp[i]);
+  next_cell<T, K>(vs, vsn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) f[i] = vs[i] * bt[i];
+  next_cell<T, K>(f, fn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const T ve = T(0.5) * (vs[i] + vsn[i]);                       // edge velocity at +1/2
+    e1[i] = ve > T(0) ? f[i] : fn[i];                             // first-order EMF
+  }
+  prev_cell<T, K>(e1, e1p);
+#pragma unroll
+  for (int i = 0; i < K; ++i) gg[i] = vs[i] * (bt[i] - hd * (e1[i] - e1p[i]));   // vs B_half
+  next_cell<T, K>(gg, ggn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) d[i] = ggn[i] - gg[i];
+  prev_cell<T, K>(d, dp);
+#pragma unroll
+  for (int i = 0; i < K; ++i) P[i] = half_vanleer(dp[i], d[i]);
+  next_cell<T, K>(P, Pn);
+  T e2[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const T ve = T(0.5) * (vs[i] + vsn[i]);
+    e2[i] = ve > T(0) ? gg[i] + P[i] : ggn[i] - Pn[i];          // limited EMF at +1/2
+  }
+  prev_cell<T, K>(e2, e2m);
+#pragma unroll
+  for (int i = 0; i < K; ++i) bt[i] = bt[i] - dth * (e2[i] - e2m[i]);
+}
+
+template <typename T, int NW, int K>
+__global__ void __launch_bounds__(32 * NW)
+ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
+  constexpr int H = 4, SEG = 32 * K - 2 * H;
+  const int lane = threadIdx.x & 31;
+  const long long wid = (long long)blockIdx.x * NW + (threadIdx.x >> 5);
+  const int nz = g.n[2], bcz = g.bc[2];
+  const int nseg = (nz + SEG - 1) / SEG;
+  const long long pencil = wid / nseg;
+  const int s0 = (int)(wid % nseg) * SEG;
+  const long long npen = (long long)g.n[0] * g.n[1];
+  const bool warp_active = pencil < npen;
+  const long long pc = warp_active ? pencil : npen - 1;
+  const int x = (int)(pc / g.n[1]), y = (int)(pc % g.n[1]);
+  const T dth = (T)(ds->dt / h);
+  const T hd = T(0.5) * dth;
+  const long long row = (long long)x * g.s[0] + (long long)y * g.s[1];
+  const TransverseOffsets o1 = transverse_offsets(x, g.n[0], g.bc[0], g.s[0]);
+  const TransverseOffsets o2 = transverse_offsets(y, g.n[1], g.bc[1], g.s[1]);
+  const int z0 = s0 - H + lane * K;
+  const T* pr = in.f[0];
+  const T* pm = in.f[3];
+  // face velocities of the four EMF rows (own and upper row, for t1 = x and t2 = y) and
+  // the transverse face fields; B_z for the constraint
+  T vo1[K], vn1[K], vo2[K], vn2[K], b1o[K], b1h[K], b2o[K], b2h[K], ba[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const long long c = row + wrap_index(z0 + i, nz, bcz);
+    T r[5], m[5];
+    r[0] = __ldg(pr + c);           m[0] = __ldg(pm + c);
+    r[1] = __ldg(pr + c + o1.lo);   m[1] = __ldg(pm + c + o1.lo);
+    r[2] = __ldg(pr + c + o1.hi);   m[2] = __ldg(pm + c + o1.hi);
+    r[3] = __ldg(pr + c + o2.lo);   m[3] = __ldg(pm + c + o2.lo);
+    r[4] = __ldg(pr + c + o2.hi);   m[4] = __ldg(pm + c + o2.hi);
+    b1o[i] = __ldg(in.f[5] + c);
+    b1h[i] = __ldg(in.f[5] + c + o1.hi);
+    b2o[i] = __ldg(in.f[6] + c);
+    b2h[i] = __ldg(in.f[6] + c + o2.hi);
+    ba[i] = __ldg(in.f[7] + c);
+    vo1[i] = Num<T>::div(m[0] + m[1], r[0] + r[1]);
+    vn1[i] = o1.hi_across_lo ? Num<T>::div(m[2] + m[1], r[2] + r[1])
+                             : Num<T>::div(m[2] + m[0], r[2] + r[0]);
+    vo2[i] = Num<T>::div(m[0] + m[3], r[0] + r[3]);
+    vn2[i] = o2.hi_across_lo ? Num<T>::div(m[4] + m[3], r[4] + r[3])
+                             : Num<T>::div(m[4] + m[0], r[4] + r[0]);
+  }
+  T eo1[K], en1[K], eo2[K], en2[K];
+  emf_seg<T, K>(vo1, b1o, dth, hd, eo1);
+  emf_seg<T, K>(vn1, b1h, dth, hd, en1);
+  emf_seg<T, K>(vo2, b2o, dth, hd, eo2);
+  emf_seg<T, K>(vn2, b2h, dth, hd, en2);
+  int st = 0;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int w = lane * K + i, z = z0 + i;
+    T bA = ba[i] + dth * (en1[i] - eo1[i]);      // constraint from t1 = x, then t2 = y
+    bA = bA + dth * (en2[i] - eo2[i]);
+    if (warp_active && w >= H && w < H + SEG && z < nz) {
+      const long long co = row + z;
+      out.f[5][co] = b1o[i];
+      out.f[6][co] = b2o[i];
+      out.f[7][co] = bA;
+      if (!(b1o[i] == b1o[i]) || !(b2o[i] == b2o[i]) || !(bA == bA)) st |= ST_NONFINITE;
+    }
+  }
+  if (st) atomicOr(&ds->status, st);
+}
+
+}  // namespace mhd
