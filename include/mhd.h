@@ -129,6 +129,31 @@ mhd_status mhd_profile_read(mhd_ctx* ctx, double ms[8], long long count[8], int 
 /* The cudaStream_t the context runs on (its own, or the one given in mhd_config). */
 mhd_status mhd_stream(const mhd_ctx* ctx, void** stream);
 
+/* FP64 sums of 8 device arrays without allocating device memory.
+ *
+ * The paper has no counterpart to this entry point.  It exists for callers that cannot
+ * call cudaMalloc: for example code inside a serving process whose device memory is all
+ * handed out by another allocator under a fixed budget, or a host thread that must not
+ * trigger the device-wide synchronisation that cudaMalloc and cudaFree imply while other
+ * work is in flight.  It computes what mhd_sums computes (the sum over n cells of each of
+ * 8 fields, accumulated in FP64) for arrays the caller owns, with the reduction's scratch
+ * held in a fixed array of 262,208 bytes in the library's device image (every GPU that
+ * loads the library keeps it until the process exits).
+ *
+ *   f       8 device pointers to n elements each, dtype 0 = float32, 1 = float64
+ *   out     host array of 8 doubles, written before the call returns
+ *   stream  cudaStream_t to run on (NULL: the default stream); the call synchronises it
+ *
+ * Returns MHD_ERR_INVALID for a NULL argument, a bad dtype, n < 1, or
+ * n > MHD_SUMS_NOALLOC_MAX_CELLS (the scratch holds one row of partial sums per 65,536
+ * cells, 4096 rows); MHD_ERR_CUDA if a CUDA call fails.  The first call on a device looks
+ * up the scratch array's device address with that device current; make that first call
+ * before any stream capture.  All calls share the one scratch array: calls whose work
+ * overlaps on the GPU race, so serialise them. */
+#define MHD_SUMS_NOALLOC_MAX_CELLS 268435456LL
+mhd_status mhd_sums_noalloc(const void* const f[8], int dtype, long long n, double out[8],
+                            void* stream);
+
 /* Free everything the context owns.  NULL is ignored. */
 void mhd_destroy(mhd_ctx* ctx);
 

@@ -24,6 +24,7 @@ UNITS = [
     # oracle's operation for operation
     ("kernels_f64.cu", ["--fmad=false"]),
     ("mhd_capi.cu", []),
+    ("mhd_noalloc.cu", []),
 ]
 
 

@@ -24,7 +24,7 @@ FP32, FP64 = 0, 1
 EXPORTS = ("mhd_create", "mhd_init_fields", "mhd_upload", "mhd_step", "mhd_apply", "mhd_cmax",
            "mhd_read", "mhd_download", "mhd_sums", "mhd_state", "mhd_set_state", "mhd_sync",
            "mhd_info", "mhd_stream", "mhd_profile", "mhd_profile_read", "mhd_destroy",
-           "mhd_status_str", "mhd_last_error")
+           "mhd_status_str", "mhd_last_error", "mhd_sums_noalloc")
 
 
 class MhdConfig(C.Structure):
@@ -70,6 +70,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "mhd_profile": ([vp, C.c_int], C.c_int),
         "mhd_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.c_int], C.c_int),
         "mhd_destroy": ([vp], None),
+        "mhd_sums_noalloc": ([C.POINTER(vp), C.c_int, C.c_longlong, dp, vp], C.c_int),
         "mhd_status_str": ([C.c_int], C.c_char_p),
         "mhd_last_error": ([vp], C.c_char_p),
     }
