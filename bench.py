@@ -41,14 +41,18 @@ FALLBACK_HBM_GBS = 6800.0
 # is 384 B per cell.
 ALG_BYTES = {"fluid": 13 * 4, "ct": 8 * 4}
 STEP_ALG_BYTES = 384
-# DRAM traffic per cell of one fluid-sweep launch from an ncu capture, keyed by the hash of
-# the kernel source it was taken on (None until captured); stale hashes report null.
-NCU_TRAFFIC = {}
+# DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
+# a step) from ncu captures on a 256^3 grid (profiles/sweep_kernels_blast256_fp32.md), keyed
+# by the hash of the kernel sources they were taken on; another hash reports null.
+NCU_TRAFFIC_PER_CELL = {"4ce521d2736026f2": 50.55}
+
+
+KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_launch_impl.cuh")
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("mhd_kernels.cuh", "mhd_launch_impl.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_0908_4362_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -310,7 +314,8 @@ def run_ours(args, world, rank, local):
     achieved = ALG_BYTES[dom] * N / (avg_ms / 1e3) / 1e9
     peak, peak_src = measured_peaks()
     src_hash = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get(src_hash)
+    tpc = NCU_TRAFFIC_PER_CELL.get(src_hash)
+    traffic = tpc * N if tpc is not None else None
     launches = sum(c for _, c in prof.values()) + 2 * sums_calls
 
     # ---- e2e: through the C ABI with pinned host buffers, copies inside the region ----
