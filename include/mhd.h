@@ -129,6 +129,48 @@ mhd_status mhd_profile_read(mhd_ctx* ctx, double ms[8], long long count[8], int 
 /* The cudaStream_t the context runs on (its own, or the one given in mhd_config). */
 mhd_status mhd_stream(const mhd_ctx* ctx, void** stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched persistent form: many grids advanced together.
+ *
+ * A batch groups FP32 contexts (any shapes, each at its own time and axis-order phase).
+ * mhd_batch_step advances every one of them by nsteps method steps (Sect. 4.2) in ONE
+ * persistent, CUDA-graph-captured kernel launch: resident CTAs take (instance, operation,
+ * tile) items from a device queue, and a per-instance completion counter makes each
+ * operation of an instance wait for all tiles of its previous operation.  Each grid's
+ * result is bit-identical to advancing it alone with mhd_step.  The contexts keep owning
+ * their state; read them with mhd_read/mhd_download as usual.
+ * ------------------------------------------------------------------------------------- */
+typedef struct mhd_batch mhd_batch;
+
+/* Create a batch over n contexts (FP32, fp64_pressure off, no t_end pending).  The
+ * contexts must outlive the batch.  z_tile_warps: warp segments per work item of a z sweep
+ * (0: 128); ctas_per_sm: resident CTAs per SM of the persistent launch (0: as many as fit).
+ * Both are launch shapes only (results do not depend on them); the autotuner picks them. */
+mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int ctas_per_sm,
+                            mhd_batch** out);
+
+/* Enqueue nsteps steps of every context of the batch as one persistent launch, ordered
+ * after each context's pending work; each context's later work waits for it.  The work
+ * list and the graph are cached per (nsteps, phases); with nsteps a multiple of 3 every
+ * call reuses them.  Returns MHD_ERR_INVALID if a context's buffers moved since creation. */
+mhd_status mhd_batch_step(mhd_batch* b, int nsteps);
+
+/* Wait for the batch.  MHD_ERR_TIMEOUT if a bounded device wait gave up (the launch then
+ * stops early and the contexts' states are incomplete). */
+mhd_status mhd_batch_sync(mhd_batch* b);
+
+/* Resident CTAs of the persistent launch, work items per launch (0 before a step) and the
+ * cudaStream_t the batch runs on (any pointer may be NULL). */
+mhd_status mhd_batch_info(const mhd_batch* b, int* resident_ctas, long long* items_per_launch,
+                          void** stream);
+
+void mhd_batch_destroy(mhd_batch* b);
+
+/* Diagnostic of the bounded device waits: launches the persistent kernel with one work item
+ * that waits for a completion nothing produces.  The wait must give up after spin_cycles
+ * SM clock cycles (1 .. 4e9) and the call returns MHD_ERR_TIMEOUT; the device stays usable. */
+mhd_status mhd_batch_selftest_timeout(long long spin_cycles);
+
 /* FP64 sums of 8 device arrays without allocating device memory.
  *
  * The paper has no counterpart to this entry point.  It exists for callers that cannot

@@ -25,6 +25,8 @@ UNITS = [
     ("kernels_f64.cu", ["--fmad=false"]),
     ("mhd_capi.cu", []),
     ("mhd_noalloc.cu", []),
+    # the batched persistent kernel runs the FP32 sweep bodies: same flags as their TU
+    ("mhd_batch.cu", ["--use_fast_math"]),
 ]
 
 

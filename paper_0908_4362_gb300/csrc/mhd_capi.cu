@@ -26,40 +26,7 @@ using mhd::FieldSet;
 using mhd::GridDesc;
 using mhd::Launch;
 
-static const int kOrder[3][3] = {{0, 1, 2}, {2, 0, 1}, {1, 2, 0}};
-
-struct mhd_ctx {
-  mhd_config cfg{};
-  GridDesc g{};
-  long long N = 0;
-  size_t esz = 4;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  void* buf[2][8] = {};
-  int cur[8] = {};
-  void* staging = nullptr;      // N doubles, host <-> device conversions
-  DevScalars* ds = nullptr;     // device
-  DevScalars* hs = nullptr;     // pinned host mirror
-  double* partial = nullptr;
-  double* sums_out = nullptr;   // device, 8 doubles
-  double* sums_host = nullptr;  // pinned, 8 doubles
-  int sum_blocks = 0;
-  int phase = 0;
-  int step = 0;
-  int steps_base = 0;           // ds->steps_done at the last synchronisation point
-  int status = 0;               // sticky ST_* bits seen at synchronisation points
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-  unsigned graph_sig[3] = {0, 0, 0};
-  long long dev_bytes = 0;
-  std::string err;
-  // kernel timing mode: steps are launched kernel by kernel with CUDA events around each
-  bool profile = false;
-  struct Pending { int kind; cudaEvent_t a, b; };
-  std::vector<Pending> pending;
-  std::vector<cudaEvent_t> free_events;
-  double prof_ms[8] = {};
-  long long prof_n[8] = {};
-};
+#include "mhd_ctx.h"
 
 // kinds: 0..2 fluid along x,y,z; 3..5 CT along x,y,z; 6 dt; 7 other
 static cudaEvent_t take_event(mhd_ctx* ctx) {
@@ -91,6 +58,7 @@ struct ProfScope {
     }
   }
 };
+
 
 static mhd_status cuda_fail(mhd_ctx* c, cudaError_t e, const char* what) {
   if (c) {

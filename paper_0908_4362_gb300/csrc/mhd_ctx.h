@@ -1,0 +1,52 @@
+// Internal: the solver context behind the opaque mhd_ctx of include/mhd.h, shared by the
+// C-ABI implementation (mhd_capi.cu) and the batched persistent form (mhd_batch.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mhd.h"
+#include "mhd_kernels.cuh"
+
+using mhd::DevScalars;
+using mhd::FieldSet;
+using mhd::GridDesc;
+
+// axis order of the forward sweep for each phase (Eq. "eq:L_sequence")
+static constexpr int kOrder[3][3] = {{0, 1, 2}, {2, 0, 1}, {1, 2, 0}};
+
+struct mhd_ctx {
+  mhd_config cfg{};
+  GridDesc g{};
+  long long N = 0;
+  size_t esz = 4;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* buf[2][8] = {};
+  int cur[8] = {};
+  void* staging = nullptr;      // N doubles, host <-> device conversions
+  DevScalars* ds = nullptr;     // device
+  DevScalars* hs = nullptr;     // pinned host mirror
+  double* partial = nullptr;
+  double* sums_out = nullptr;   // device, 8 doubles
+  double* sums_host = nullptr;  // pinned, 8 doubles
+  int sum_blocks = 0;
+  int phase = 0;
+  int step = 0;
+  int steps_base = 0;           // ds->steps_done at the last synchronisation point
+  int status = 0;               // sticky ST_* bits seen at synchronisation points
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  unsigned graph_sig[3] = {0, 0, 0};
+  long long dev_bytes = 0;
+  std::string err;
+  // kernel timing mode: steps are launched kernel by kernel with CUDA events around each
+  bool profile = false;
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  double prof_ms[8] = {};
+  long long prof_n[8] = {};
+};
+

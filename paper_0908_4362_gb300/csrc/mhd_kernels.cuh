@@ -253,7 +253,7 @@ __global__ void cmax_kernel(GridDesc g, FieldSet<T> in, T gamma, DevScalars* ds)
 
 // dt = cfl h / c_max on the device, clipped to land on t_end (Sect. 4.2 steps 4-5, 8-9)
 template <typename T>
-__global__ void dt_kernel(DevScalars* ds, double cfl_h) {
+__device__ __forceinline__ void dt_update(DevScalars* ds, double cfl_h) {
   const double cm = Num<T>::from_bits(ds->cmax);
   double dt = cfl_h / cm;
   int clipped = 0, active = 1;
@@ -278,6 +278,11 @@ __global__ void dt_kernel(DevScalars* ds, double cfl_h) {
     ds->steps_done += 1;
   }
   ds->cmax = 0ull;   // the last sweep of this step accumulates the next c_max
+}
+
+template <typename T>
+__global__ void dt_kernel(DevScalars* ds, double cfl_h) {
+  dt_update<T>(ds, cfl_h);
 }
 
 // FP64 conservation sums: per-block partial sums (deterministic two-pass reduction)

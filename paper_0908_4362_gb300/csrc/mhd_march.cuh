@@ -131,17 +131,21 @@ constexpr int kMarchRing = kMarchDepth + 1;
 // z fastest (coalesced rows per field); each thread marches its pencil over S cells plus
 // the 6-cell halo.  blockIdx.y selects the tile along the sweep.
 // ------------------------------------------------------------------------------------
+// one tile: pencils bx*NT .. bx*NT+NT-1 of the transverse plane, cells by*S .. by*S+S-1
+// along the sweep; smem_raw holds the prefetch ring (march_ring_bytes)
 template <typename T, int A, bool LAST, bool P64, int S, int NT>
-__global__ void __launch_bounds__(NT)
-fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
+__device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const FieldSet<T>& in,
+                                                    const FieldSet<T>& out, T gamma, double h,
+                                                    DevScalars* ds, unsigned bx, unsigned by,
+                                                    unsigned char* smem_raw) {
   static_assert(A == 0 || A == 1, "x or y sweep");
   constexpr int O = (A == 0) ? 1 : 0;       // the transverse axis that is not z
   constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
-  const long long p = (long long)blockIdx.x * NT + threadIdx.x;
+  const long long p = (long long)bx * NT + threadIdx.x;
   const int z = (int)(p % g.n[2]);
   const long long o_ = p / g.n[2];
   const int o = (int)(o_ < g.n[O] ? o_ : g.n[O]);
-  const int a0 = blockIdx.y * S;
+  const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
   const bool active = o_ < g.n[O];
   const T dth = (T)(ds->dt / h);
@@ -168,7 +172,6 @@ fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, D
   const int js = a0 - 3;
   const int kend = min(S, nA - a0) + 6;       // iterations needed for this tile
   // shared ring: [slot][value][thread], 10 values per iteration (u, B_n(j+1), B_t1 x2, B_t2 x2)
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);
   constexpr int NV = 10;
   auto issue = [&](int kk) {
@@ -231,6 +234,14 @@ fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, D
   cp_async_wait<0>();
   if (LAST) block_max_to_global(cm, nan_seen, ds);
   if (active && P.st) atomicOr(&ds->status, P.st);
+}
+
+template <typename T, int A, bool LAST, bool P64, int S, int NT>
+__global__ void __launch_bounds__(NT)
+fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fluid_march_xy_tile<T, A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, blockIdx.x, blockIdx.y,
+                                              smem_raw);
 }
 
 }  // namespace mhd
@@ -339,16 +350,17 @@ struct CtColumn {
 
 // x or y sweep of the constrained transport; thread layout as fluid_march_xy
 template <typename T, int A, int S, int NT>
-__global__ void __launch_bounds__(NT)
-ct_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
+__device__ __forceinline__ void ct_march_xy_tile(const GridDesc& g, const FieldSet<T>& in,
+                                                 const FieldSet<T>& out, double h, DevScalars* ds,
+                                                 unsigned bx, unsigned by, unsigned char* smem_raw) {
   static_assert(A == 0 || A == 1, "x or y sweep");
   constexpr int O = (A == 0) ? 1 : 0;
   constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
-  const long long p = (long long)blockIdx.x * NT + threadIdx.x;
+  const long long p = (long long)bx * NT + threadIdx.x;
   const int z = (int)(p % g.n[2]);
   const long long o_ = p / g.n[2];
   const int oc = (int)(o_ < g.n[O] ? o_ : g.n[O] - 1);
-  const int a0 = blockIdx.y * S;
+  const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
   const bool active = o_ < g.n[O];
   const T dth = (T)(ds->dt / h);
@@ -367,7 +379,6 @@ ct_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* d
   col.init();
   const int js = a0 - 4;
   const int kend = min(S, nA - a0) + 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);
   constexpr int NV = 15;
   auto issue = [&](int kk) {
@@ -419,6 +430,13 @@ ct_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* d
   }
   cp_async_wait<0>();
   if (active && st) atomicOr(&ds->status, st);
+}
+
+template <typename T, int A, int S, int NT>
+__global__ void __launch_bounds__(NT)
+ct_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ct_march_xy_tile<T, A, S, NT>(g, in, out, h, ds, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 }  // namespace mhd

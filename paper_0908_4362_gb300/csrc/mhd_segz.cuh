@@ -12,6 +12,14 @@
 
 namespace mhd {
 
+// global loads: the read-only path in standalone kernels (NC), plain coherent loads where
+// the same launch writes the data earlier (the persistent batched kernel)
+template <bool NC, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (NC) return __ldg(p);
+  else return *p;
+}
+
 template <typename T>
 __device__ __forceinline__ T shdown(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 template <typename T>
@@ -32,12 +40,13 @@ __device__ __forceinline__ void prev_cell(const T (&x)[K], T (&xp)[K]) {
   for (int i = 0; i < K; ++i) xp[i] = (i > 0) ? x[i - 1] : from_prev_lane;
 }
 
-template <typename T, bool LAST, bool P64, int NW, int K>
-__global__ void __launch_bounds__(32 * NW)
-fluid_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
+// one warp: segment `wid` (pencil wid / nseg, segment wid % nseg); all 32 lanes call it
+template <typename T, bool LAST, bool P64, int K, bool NC>
+__device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
+                                                 const FieldSet<T>& out, T gamma, double h,
+                                                 DevScalars* ds, long long wid) {
   constexpr int H = 3, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
-  const long long wid = (long long)blockIdx.x * NW + (threadIdx.x >> 5);
   const int nz = g.n[2], bcz = g.bc[2];
   const int nseg = (nz + SEG - 1) / SEG;
   const long long pencil = wid / nseg;
@@ -58,14 +67,14 @@ fluid_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevS
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const int zc = wrap_index(z0 + i, nz, bcz), zn = wrap_index(z0 + i + 1, nz, bcz);
-    u[i][0] = __ldg(in.f[0] + row + zc);
-    u[i][1] = __ldg(in.f[3] + row + zc);
-    u[i][2] = __ldg(in.f[1] + row + zc);
-    u[i][3] = __ldg(in.f[2] + row + zc);
-    u[i][4] = __ldg(in.f[4] + row + zc);
-    b[i][0] = T(0.5) * (__ldg(in.f[7] + row + zc) + __ldg(in.f[7] + row + zn));
-    b[i][1] = T(0.5) * (__ldg(in.f[5] + row + zc) + __ldg(in.f[5] + r1 + zc));
-    b[i][2] = T(0.5) * (__ldg(in.f[6] + row + zc) + __ldg(in.f[6] + r2 + zc));
+    u[i][0] = ldx<NC>(in.f[0] + row + zc);
+    u[i][1] = ldx<NC>(in.f[3] + row + zc);
+    u[i][2] = ldx<NC>(in.f[1] + row + zc);
+    u[i][3] = ldx<NC>(in.f[2] + row + zc);
+    u[i][4] = ldx<NC>(in.f[4] + row + zc);
+    b[i][0] = T(0.5) * (ldx<NC>(in.f[7] + row + zc) + ldx<NC>(in.f[7] + row + zn));
+    b[i][1] = T(0.5) * (ldx<NC>(in.f[5] + row + zc) + ldx<NC>(in.f[5] + r1 + zc));
+    b[i][2] = T(0.5) * (ldx<NC>(in.f[6] + row + zc) + ldx<NC>(in.f[6] + r2 + zc));
   }
   // stage 1: first-order fluxes, half step
   T uh[K][5];
@@ -148,6 +157,13 @@ fluid_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevS
   if (warp_active && st) atomicOr(&ds->status, st);
 }
 
+template <typename T, bool LAST, bool P64, int NW, int K>
+__global__ void __launch_bounds__(32 * NW)
+fluid_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
+  fluid_seg_z_warp<T, LAST, P64, K, true>(g, in, out, gamma, h, ds,
+                                          (long long)blockIdx.x * NW + (threadIdx.x >> 5));
+}
+
 // one EMF pipeline over the window: bt[] becomes the advected B_t (valid on window cells
 // 4 .. 32K-5) and e2m[] the limited EMF at each cell's lower face (4 .. 32K-4)
 template <typename T, int K>
@@ -187,12 +203,12 @@ __device__ __forceinline__ void emf_seg(const T (&vf)[K], T (&bt)[K], T dth, T h
   for (int i = 0; i < K; ++i) bt[i] = bt[i] - dth * (e2[i] - e2m[i]);
 }
 
-template <typename T, int NW, int K>
-__global__ void __launch_bounds__(32 * NW)
-ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
+template <typename T, int K, bool NC>
+__device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
+                                              const FieldSet<T>& out, double h, DevScalars* ds,
+                                              long long wid) {
   constexpr int H = 4, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
-  const long long wid = (long long)blockIdx.x * NW + (threadIdx.x >> 5);
   const int nz = g.n[2], bcz = g.bc[2];
   const int nseg = (nz + SEG - 1) / SEG;
   const long long pencil = wid / nseg;
@@ -216,16 +232,16 @@ ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) 
   for (int i = 0; i < K; ++i) {
     const long long c = row + wrap_index(z0 + i, nz, bcz);
     T r[5], m[5];
-    r[0] = __ldg(pr + c);           m[0] = __ldg(pm + c);
-    r[1] = __ldg(pr + c + o1.lo);   m[1] = __ldg(pm + c + o1.lo);
-    r[2] = __ldg(pr + c + o1.hi);   m[2] = __ldg(pm + c + o1.hi);
-    r[3] = __ldg(pr + c + o2.lo);   m[3] = __ldg(pm + c + o2.lo);
-    r[4] = __ldg(pr + c + o2.hi);   m[4] = __ldg(pm + c + o2.hi);
-    b1o[i] = __ldg(in.f[5] + c);
-    b1h[i] = __ldg(in.f[5] + c + o1.hi);
-    b2o[i] = __ldg(in.f[6] + c);
-    b2h[i] = __ldg(in.f[6] + c + o2.hi);
-    ba[i] = __ldg(in.f[7] + c);
+    r[0] = ldx<NC>(pr + c);           m[0] = ldx<NC>(pm + c);
+    r[1] = ldx<NC>(pr + c + o1.lo);   m[1] = ldx<NC>(pm + c + o1.lo);
+    r[2] = ldx<NC>(pr + c + o1.hi);   m[2] = ldx<NC>(pm + c + o1.hi);
+    r[3] = ldx<NC>(pr + c + o2.lo);   m[3] = ldx<NC>(pm + c + o2.lo);
+    r[4] = ldx<NC>(pr + c + o2.hi);   m[4] = ldx<NC>(pm + c + o2.hi);
+    b1o[i] = ldx<NC>(in.f[5] + c);
+    b1h[i] = ldx<NC>(in.f[5] + c + o1.hi);
+    b2o[i] = ldx<NC>(in.f[6] + c);
+    b2h[i] = ldx<NC>(in.f[6] + c + o2.hi);
+    ba[i] = ldx<NC>(in.f[7] + c);
     vo1[i] = Num<T>::div(m[0] + m[1], r[0] + r[1]);
     vn1[i] = o1.hi_across_lo ? Num<T>::div(m[2] + m[1], r[2] + r[1])
                              : Num<T>::div(m[2] + m[0], r[2] + r[0]);
@@ -253,6 +269,12 @@ ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) 
     }
   }
   if (st) atomicOr(&ds->status, st);
+}
+
+template <typename T, int NW, int K>
+__global__ void __launch_bounds__(32 * NW)
+ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
+  ct_seg_z_warp<T, K, true>(g, in, out, h, ds, (long long)blockIdx.x * NW + (threadIdx.x >> 5));
 }
 
 }  // namespace mhd

@@ -24,7 +24,9 @@ FP32, FP64 = 0, 1
 EXPORTS = ("mhd_create", "mhd_init_fields", "mhd_upload", "mhd_step", "mhd_apply", "mhd_cmax",
            "mhd_read", "mhd_download", "mhd_sums", "mhd_state", "mhd_set_state", "mhd_sync",
            "mhd_info", "mhd_stream", "mhd_profile", "mhd_profile_read", "mhd_destroy",
-           "mhd_status_str", "mhd_last_error", "mhd_sums_noalloc")
+           "mhd_status_str", "mhd_last_error", "mhd_sums_noalloc", "mhd_batch_create",
+           "mhd_batch_step", "mhd_batch_sync", "mhd_batch_info", "mhd_batch_destroy",
+           "mhd_batch_selftest_timeout")
 
 
 class MhdConfig(C.Structure):
@@ -71,6 +73,12 @@ def load_library(path: str | None = None) -> C.CDLL:
         "mhd_profile_read": ([vp, dp, C.POINTER(C.c_longlong), C.c_int], C.c_int),
         "mhd_destroy": ([vp], None),
         "mhd_sums_noalloc": ([C.POINTER(vp), C.c_int, C.c_longlong, dp, vp], C.c_int),
+        "mhd_batch_create": ([C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
+        "mhd_batch_step": ([vp, C.c_int], C.c_int),
+        "mhd_batch_sync": ([vp], C.c_int),
+        "mhd_batch_info": ([vp, ip, C.POINTER(C.c_longlong), C.POINTER(vp)], C.c_int),
+        "mhd_batch_destroy": ([vp], None),
+        "mhd_batch_selftest_timeout": ([C.c_longlong], C.c_int),
         "mhd_status_str": ([C.c_int], C.c_char_p),
         "mhd_last_error": ([vp], C.c_char_p),
     }
@@ -243,3 +251,50 @@ class Solver:
         s = C.c_void_p()
         self._check(self.lib.mhd_stream(self.ctx, C.byref(s)), "mhd_stream")
         return s.value or 0
+
+
+class Batch:
+    """Many solvers advanced together by one persistent launch per step call
+    (mhd_batch_create / mhd_batch_step / mhd_batch_sync / mhd_batch_destroy)."""
+
+    def __init__(self, solvers, z_tile_warps: int = 0, ctas_per_sm: int = 0):
+        self.lib = load_library()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx for s in self.solvers])
+        h_ = C.c_void_p()
+        st = self.lib.mhd_batch_create(arr, len(self.solvers), int(z_tile_warps), int(ctas_per_sm),
+                                       C.byref(h_))
+        if st != MHD_OK:
+            raise MhdError(st, f"mhd_batch_create: {self.lib.mhd_status_str(st).decode()}")
+        self.b = h_
+
+    def step(self, nsteps: int):
+        st = self.lib.mhd_batch_step(self.b, int(nsteps))
+        if st != MHD_OK:
+            raise MhdError(st, f"mhd_batch_step: {self.lib.mhd_status_str(st).decode()}")
+
+    def sync(self) -> int:
+        return self.lib.mhd_batch_sync(self.b)
+
+    def info(self):
+        c, n, s = C.c_int(), C.c_longlong(), C.c_void_p()
+        self.lib.mhd_batch_info(self.b, C.byref(c), C.byref(n), C.byref(s))
+        return c.value, n.value
+
+    def stream_handle(self) -> int:
+        s = C.c_void_p()
+        self.lib.mhd_batch_info(self.b, None, None, C.byref(s))
+        return s.value or 0
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mhd_batch_destroy(self.b)
+            self.b = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

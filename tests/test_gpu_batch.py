@@ -1,0 +1,68 @@
+"""The batched persistent form (mhd_batch_*): many uneven grids advanced by one persistent
+launch give, for every grid, the same bits as advancing it alone with mhd_step; and the
+bounded device wait of the persistent kernel gives up with MHD_ERR_TIMEOUT."""
+import numpy as np
+import pytest
+
+from paper_0908_4362_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mhd():
+    from paper_0908_4362_gb300 import build, mhd as m
+    build.build()
+    m.load_library()
+    return m
+
+
+def _problems():
+    # small uneven instances of the batched workload, one with mixed boundaries, one 2D
+    probs = [I.batched_instance(i, lo=12, hi=40) for i in range(5)]
+    probs.append(I.random_smooth((21, 9, 30), seed=21, bc=(1, 0, 1)))
+    probs.append(I.orszag_tang(40, ny=28))
+    return probs
+
+
+@pytest.mark.parametrize("nsteps", [3, 4])
+def test_batch_matches_alone_bitwise(mhd, nsteps):
+    probs = _problems()
+    pre = [0, 1, 2, 0, 1, 2, 1]          # instances start at different axis-order phases
+    alone = []
+    for p, k in zip(probs, pre):
+        with mhd.Solver.from_problem(p, prec=mhd.FP32) as s:
+            s.step(k + 2 * nsteps, sync=True)
+            alone.append(s.read())
+    solvers = [mhd.Solver.from_problem(p, prec=mhd.FP32) for p in probs]
+    for s, k in zip(solvers, pre):
+        if k:
+            s.step(k, sync=True)
+    with mhd.Batch(solvers, z_tile_warps=16) as b:
+        b.step(nsteps)
+        b.step(nsteps)                    # a second launch (reused or rebuilt work list)
+        assert b.sync() == mhd.MHD_OK
+        ctas, items = b.info()
+        assert ctas > 0 and items > 0
+    for s, ref, k in zip(solvers, alone, pre):
+        got = s.read()
+        t, _, stp, ph = s.state()
+        assert stp == k + 2 * nsteps and ph == (k + 2 * nsteps) % 3
+        assert np.array_equal(got, ref)
+        s.close()
+
+
+def test_batch_rejects_fp64_context(mhd):
+    s = mhd.Solver.from_problem(I.random_smooth((8, 8, 8), seed=3), prec=mhd.FP64)
+    with pytest.raises(mhd.MhdError):
+        mhd.Batch([s])
+    s.close()
+
+
+def test_bounded_wait_times_out(mhd):
+    lib = mhd.load_library()
+    # ~10 ms of SM clock, then the wait gives up and reports it
+    assert lib.mhd_batch_selftest_timeout(20_000_000) == mhd.MHD_ERR_TIMEOUT
+    # the device is still usable afterwards
+    with mhd.Solver.from_problem(I.random_smooth((10, 10, 10), seed=4), prec=mhd.FP32) as s:
+        s.step(2, sync=True)
