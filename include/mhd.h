@@ -144,7 +144,7 @@ typedef struct mhd_batch mhd_batch;
 
 /* Create a batch over n contexts (FP32, fp64_pressure off, no t_end pending).  The
  * contexts must outlive the batch.  z_tile_warps: warp segments per work item of a z sweep
- * (0: 128); ctas_per_sm: resident CTAs per SM of the persistent launch (0: as many as fit).
+ * (0: chosen per sweep, about 1024 items, 4 to 128 segments each); ctas_per_sm: resident CTAs per SM of the persistent launch (0: as many as fit).
  * Both are launch shapes only (results do not depend on them); the autotuner picks them. */
 mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int ctas_per_sm,
                             mhd_batch** out);
@@ -154,6 +154,15 @@ mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int c
  * list and the graph are cached per (nsteps, phases); with nsteps a multiple of 3 every
  * call reuses them.  Returns MHD_ERR_INVALID if a context's buffers moved since creation. */
 mhd_status mhd_batch_step(mhd_batch* b, int nsteps);
+
+/* As mhd_batch_step, with a step count per context: nsteps[i] >= 0 for each of the n
+ * contexts (in creation order), at least one of them >= 1; a context with 0 is left as it
+ * is.  Work items are queued step by step, so a context with more steps keeps advancing
+ * after the others have finished within the same launch.  Used by a scheduler that gives
+ * small grids many steps and large grids few in one launch.  The work list and graph are
+ * cached for the last (counts, phases) key only.  MHD_ERR_INVALID for a negative count,
+ * all counts 0, or moved buffers. */
+mhd_status mhd_batch_step_each(mhd_batch* b, const int* nsteps);
 
 /* Wait for the batch.  MHD_ERR_TIMEOUT if a bounded device wait gave up (the launch then
  * stops early and the contexts' states are incomplete). */

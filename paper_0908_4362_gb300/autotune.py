@@ -13,7 +13,8 @@ from . import build as _build
 from . import mhd
 
 CACHE = os.path.join(_build.BUILD, "autotune.json")
-CANDIDATES = [(w, c) for w in (32, 64, 128, 256) for c in (0, 2)]
+# z_tile_warps 0 = chosen per sweep by the library (about 1024 items per z sweep)
+CANDIDATES = [(w, c) for w in (0, 32, 64, 128, 256) for c in (0, 2)]
 
 
 def _key(shapes, nsteps: int) -> str:

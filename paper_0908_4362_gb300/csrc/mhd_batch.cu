@@ -24,6 +24,7 @@
 
 #include "../../include/mhd.h"
 #include "mhd_ctx.h"
+#include "mhd_flat.cuh"
 #include "mhd_march.cuh"
 #include "mhd_segz.cuh"
 
@@ -31,14 +32,21 @@ namespace mhd {
 
 constexpr int kBatchNT = 128;     // threads per CTA (all bodies use 128)
 constexpr int kBatchS = 64;       // march tile length along the sweep
-constexpr int kBatchK = 2;        // cells per lane of the z segments
+constexpr int kBatchK = 3;        // cells per lane of the z segments
 constexpr long long kSpinCycles = 4000000000LL;   // ~2 s of SM clock per wait
-enum : int { OP_DT = 0, OP_FLUID = 1, OP_CT = 2 };
+constexpr int kFlatCells = kBatchNT * 16;   // cells per item of the per-cell operations
+constexpr long long kAutoTiles = 1024;      // target items per z sweep when not set
+// OP_NOP: a fluid sweep along a flat axis (identity, no items); OP_CMAX: c_max of the state
+// (the last fluid sweep of a step along a flat axis); OP_CTFLAT: CT along a flat axis
+enum : int { OP_DT = 0, OP_FLUID = 1, OP_CT = 2, OP_NOP = 3, OP_CMAX = 4, OP_CTFLAT = 5 };
+
+constexpr int kBatchRowsR = kBatchNT / 32;   // warps of a shared-row CT tile
 
 struct BatchOp {
   FieldSet<float> in, out;
   GridDesc g;
   int kind, axis, last;
+  int rows;            // CT x/y in the shared-row form (ct_rows_xy_tile)
   int gx;              // march: tiles across the transverse plane (tile = by * gx + bx)
   int wpt;             // z segments: warp segments per tile
   long long nwarps;    // z segments: warp segments of the sweep
@@ -91,10 +99,17 @@ template <int A>
 __device__ __forceinline__ void batch_ct_xy(const BatchOp& op, const BatchInst& in, unsigned tile,
                                             unsigned char* smem) {
   const unsigned bx = tile % op.gx, by = tile / op.gx;
-  ct_march_xy_tile<float, A, kBatchS, kBatchNT>(op.g, op.in, op.out, in.h, in.ds, bx, by, smem);
+  if (op.rows)
+    ct_rows_xy_tile<float, A, kBatchS, kBatchRowsR>(op.g, op.in, op.out, in.h, in.ds, bx, by,
+                                                    smem);
+  else
+    ct_march_xy_tile<float, A, kBatchS, kBatchNT>(op.g, op.in, op.out, in.h, in.ds, bx, by, smem);
 }
 
-__global__ void __launch_bounds__(kBatchNT) batch_kernel(BatchArgs a) {
+#ifndef MHD_BATCH_MINB
+#define MHD_BATCH_MINB 3
+#endif
+__global__ void __launch_bounds__(kBatchNT, MHD_BATCH_MINB) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_id;
   __shared__ int s_go;
@@ -104,16 +119,22 @@ __global__ void __launch_bounds__(kBatchNT) batch_kernel(BatchArgs a) {
       int go = id < a.nitems ? 1 : 0;
       if (go) {
         const BatchItem it = a.items[id];
-        const long long t0 = clock64();
-        while (ld_acquire(a.done + it.inst) < it.need) {
-          if (ld_relaxed(a.abort)) { go = 0; break; }
-          if (clock64() - t0 > a.spin_limit) {
-            atomicOr(a.status, 1);
-            atomicExch(a.abort, 1);
-            go = 0;
-            break;
+        // poll with relaxed loads (cheaper than GPU-scope acquire loads, which must order
+        // every later load of the SM), then one acquire load once the count is reached: it
+        // reads a value of the counter's release sequence
+        if (ld_acquire(a.done + it.inst) < it.need) {
+          const long long t0 = clock64();
+          while (ld_relaxed(a.done + it.inst) < it.need) {
+            if (ld_relaxed(a.abort)) { go = 0; break; }
+            if (clock64() - t0 > a.spin_limit) {
+              atomicOr(a.status, 1);
+              atomicExch(a.abort, 1);
+              go = 0;
+              break;
+            }
+            __nanosleep(64);
           }
-          __nanosleep(64);
+          if (go) (void)ld_acquire(a.done + it.inst);
         }
       }
       s_id = id;
@@ -127,6 +148,23 @@ __global__ void __launch_bounds__(kBatchNT) batch_kernel(BatchArgs a) {
     const int warp = threadIdx.x >> 5;
     if (op.kind == OP_DT) {
       if (threadIdx.x == 0) dt_update<float>(ins.ds, ins.cfl_h);
+    } else if (op.kind == OP_CMAX || op.kind == OP_CTFLAT) {
+      const long long N = (long long)op.g.n[0] * op.g.n[1] * op.g.n[2];
+      const long long i0 = (long long)it.tile * kFlatCells;
+      const long long i1 = min(i0 + kFlatCells, N);
+      if (op.kind == OP_CMAX) {
+        cmax_range<float, false>(op.g, op.in, ins.gamma, ins.ds, i0 + threadIdx.x, i1, kBatchNT);
+      } else {
+        const float dth = (float)(ins.ds->dt / ins.h);
+        int st;
+        if (op.axis == 0)
+          st = ct_flat_range<float, 0>(op.g, op.in, op.out, dth, i0 + threadIdx.x, i1, kBatchNT);
+        else if (op.axis == 1)
+          st = ct_flat_range<float, 1>(op.g, op.in, op.out, dth, i0 + threadIdx.x, i1, kBatchNT);
+        else
+          st = ct_flat_range<float, 2>(op.g, op.in, op.out, dth, i0 + threadIdx.x, i1, kBatchNT);
+        if (st) atomicOr(&ins.ds->status, st);
+      }
     } else if (op.axis < 2) {
       if (op.kind == OP_FLUID) {
         if (op.axis == 0) batch_fluid_xy<0>(op, ins, it.tile, smem_raw);
@@ -172,7 +210,7 @@ struct mhd_batch {
   std::vector<BatchOp> ops;            // [instance][phase][13]
   cudaStream_t stream = nullptr;
   int grid = 0;                        // resident CTAs of the persistent launch
-  int wpt = 128;                       // z warp segments per tile
+  int wpt = 0;                         // z warp segments per tile (0: chosen per sweep)
   size_t smem = 0;
   BatchOp* d_ops = nullptr;
   BatchInst* d_inst = nullptr;
@@ -222,13 +260,20 @@ static void build_step_ops(const mhd_ctx* c, int phase, int wpt, BatchOp* out) {
     if (op.axis < 2) {
       const int o = op.axis == 0 ? 1 : 0;
       const long long np = (long long)g.n[2] * g.n[o];
-      op.gx = (int)((np + mhd::kBatchNT - 1) / mhd::kBatchNT);
+      op.rows = (op.kind == mhd::OP_CT && mhd::ct_use_rows(g, op.axis)) ? 1 : 0;
+      op.gx = op.rows ? ((g.n[2] + 30) / 31) * ((g.n[o] + mhd::kBatchRowsR - 2) /
+                                                (mhd::kBatchRowsR - 1))
+                      : (int)((np + mhd::kBatchNT - 1) / mhd::kBatchNT);
       op.tiles = op.gx * ((g.n[op.axis] + mhd::kBatchS - 1) / mhd::kBatchS);
     } else {
       const int seg = 32 * mhd::kBatchK - (op.kind == mhd::OP_FLUID ? 6 : 8);
       op.nwarps = (long long)g.n[0] * g.n[1] * ((g.n[2] + seg - 1) / seg);
-      op.wpt = wpt;
-      op.tiles = (int)((op.nwarps + wpt - 1) / wpt);
+      // 0: about kAutoTiles items per z sweep (small grids get short items, large ones
+      // up to 128 warp segments each)
+      long long w = wpt > 0 ? wpt : (op.nwarps + mhd::kAutoTiles - 1) / mhd::kAutoTiles;
+      w = w < 4 ? 4 : (w > 128 && wpt == 0 ? 128 : w);
+      op.wpt = (int)w;
+      op.tiles = (int)((op.nwarps + w - 1) / w);
     }
   };
   int n = 0;
@@ -241,8 +286,21 @@ static void build_step_ops(const mhd_ctx* c, int phase, int wpt, BatchOp* out) {
     op.last = last ? 1 : 0;
     op.in = fs(false);
     op.out = fs(true);
+    const long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    const int flat_tiles = (int)((ncell + mhd::kFlatCells - 1) / mhd::kFlatCells);
     if (kind == mhd::OP_DT) {
       op.tiles = 1;
+    } else if (mhd::axis_is_flat(c->g, axis)) {
+      // along a flat axis (mhd_flat.cuh): the fluid sweep is the identity, the CT changes B_A
+      if (kind == mhd::OP_FLUID) {
+        op.kind = last ? mhd::OP_CMAX : mhd::OP_NOP;
+        op.tiles = last ? flat_tiles : 0;
+        op.out = op.in;
+      } else {
+        op.kind = mhd::OP_CTFLAT;
+        op.tiles = flat_tiles;
+        cur[5 + axis] ^= 1;
+      }
     } else {
       geometry(op);
       if (kind == mhd::OP_FLUID) for (int k = 0; k < 5; ++k) cur[k] ^= 1;
@@ -290,7 +348,7 @@ mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int c
     if (!c || c->esz != 4 || c->cfg.fp64_pressure) return MHD_ERR_INVALID;
   }
   mhd_batch* b = new mhd_batch();
-  b->wpt = z_tile_warps > 0 ? z_tile_warps : 128;
+  b->wpt = z_tile_warps > 0 ? z_tile_warps : 0;
   b->ctx.assign(ctxs, ctxs + n);
   b->sig.resize(n);
   b->ops.resize((size_t)n * 3 * kOpsPerStep);
@@ -339,16 +397,20 @@ mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int c
 }
 
 // Advance every instance by nsteps steps in one persistent launch.
-mhd_status mhd_batch_step(mhd_batch* b, int nsteps) {
-  if (!b || nsteps < 1) return MHD_ERR_INVALID;
+// One persistent launch advancing instance i by nsteps[i] steps (0 leaves it as it is).
+static mhd_status batch_step_counts(mhd_batch* b, const int* nsteps) {
   const int n = (int)b->ctx.size();
+  int smax = 0;
   std::vector<int> key;
-  key.push_back(nsteps);
   for (int i = 0; i < n; ++i) {
     mhd_ctx* c = b->ctx[i];
+    if (nsteps[i] < 0) return MHD_ERR_INVALID;
     if (ctx_sig(c) != b->sig[i]) return MHD_ERR_INVALID;   // buffers moved (mhd_apply)
+    smax = nsteps[i] > smax ? nsteps[i] : smax;
+    key.push_back(nsteps[i]);
     key.push_back(c->phase);
   }
+  if (smax < 1) return MHD_ERR_INVALID;
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     // the previous launch may still read the current work list: let it finish first
@@ -356,9 +418,10 @@ mhd_status mhd_batch_step(mhd_batch* b, int nsteps) {
     // items: round by round (step, operation), all instances of a round together
     std::vector<BatchItem> items;
     std::vector<int> need(n, 0);
-    for (int s = 0; s < nsteps; ++s)
+    for (int s = 0; s < smax; ++s)
       for (int k = 0; k < kOpsPerStep; ++k)
         for (int i = 0; i < n; ++i) {
+          if (s >= nsteps[i]) continue;
           const int p = (b->ctx[i]->phase + s) % 3;
           const int opi = (i * 3 + p) * kOpsPerStep + k;
           const int tiles = b->ops[opi].tiles;
@@ -414,11 +477,22 @@ mhd_status mhd_batch_step(mhd_batch* b, int nsteps) {
   for (int i = 0; i < n; ++i) {
     BK(cudaStreamWaitEvent(b->ctx[i]->stream, b->ev, 0), "wait event");
     mhd_ctx* c = b->ctx[i];
-    c->phase = (c->phase + nsteps) % 3;
-    c->step += nsteps;
-    c->steps_base += nsteps;
+    c->phase = (c->phase + nsteps[i]) % 3;
+    c->step += nsteps[i];
+    c->steps_base += nsteps[i];
   }
   return MHD_OK;
+}
+
+mhd_status mhd_batch_step(mhd_batch* b, int nsteps) {
+  if (!b || nsteps < 1) return MHD_ERR_INVALID;
+  std::vector<int> counts(b->ctx.size(), nsteps);
+  return batch_step_counts(b, counts.data());
+}
+
+mhd_status mhd_batch_step_each(mhd_batch* b, const int* nsteps) {
+  if (!b || !nsteps) return MHD_ERR_INVALID;
+  return batch_step_counts(b, nsteps);
 }
 
 // Wait for the batch's stream; MHD_ERR_TIMEOUT if a bounded wait gave up.

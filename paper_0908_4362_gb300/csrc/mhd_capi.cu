@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/mhd.h"
+#include "mhd_flat.cuh"
 #include "mhd_kernels.cuh"
 #include "mhd_launch.h"
 
@@ -92,7 +93,8 @@ static cudaError_t enqueue_fluid(mhd_ctx* ctx, int axis, bool last) {
   FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
   cudaError_t e = Launch<T>::fluid(ctx->g, in, out, ctx->cfg.gamma, ctx->cfg.h, ctx->ds, axis,
                                    last, ctx->cfg.fp64_pressure != 0, ctx->stream);
-  for (int k = 0; k < 5; ++k) ctx->cur[k] ^= 1;
+  if (!mhd::axis_is_flat(ctx->g, axis))   // along a flat axis the sweep is the identity
+    for (int k = 0; k < 5; ++k) ctx->cur[k] ^= 1;
   return e;
 }
 
@@ -101,7 +103,8 @@ static cudaError_t enqueue_ct(mhd_ctx* ctx, int axis) {
   ProfScope ps(ctx, 3 + axis);
   FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
   cudaError_t e = Launch<T>::ct(ctx->g, in, out, ctx->cfg.h, ctx->ds, axis, ctx->stream);
-  for (int k = 5; k < 8; ++k) ctx->cur[k] ^= 1;
+  if (mhd::axis_is_flat(ctx->g, axis)) ctx->cur[5 + axis] ^= 1;   // only B_A changes
+  else for (int k = 5; k < 8; ++k) ctx->cur[k] ^= 1;
   return e;
 }
 

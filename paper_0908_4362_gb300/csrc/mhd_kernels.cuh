@@ -51,6 +51,8 @@ struct DevScalars {
 template <typename T> struct Num;
 template <> struct Num<float> {
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  // a rounded product that the compiler never fuses into a following add
+  static __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float sqrt(float a) { return sqrtf(a); }
   static __device__ __forceinline__ unsigned long long bits(float v) {
     return (unsigned long long)__float_as_uint(v);
@@ -65,6 +67,7 @@ template <> struct Num<float> {
 };
 template <> struct Num<double> {
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
   static __device__ __forceinline__ unsigned long long bits(double v) {
     return (unsigned long long)__double_as_longlong(v);
@@ -223,32 +226,48 @@ __host__ __device__ constexpr int axis_t2(int a) { return (a + 2) % 3; }
 // auxiliary kernels
 // ------------------------------------------------------------------------------------
 
-// c_max of a state (used at initialisation and on request)
+// CFL speed of cell i of a state, with B averaged from the faces to the cell centre
 template <typename T, bool P64>
-__global__ void cmax_kernel(GridDesc g, FieldSet<T> in, T gamma, DevScalars* ds) {
-  const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+__device__ __forceinline__ T cmax_cell(const GridDesc& g, const FieldSet<T>& in, long long i,
+                                       T gamma, int* st) {
+  const int z = (int)(i % g.n[2]);
+  const long long xy = i / g.n[2];
+  const int y = (int)(xy % g.n[1]);
+  const int x = (int)(xy / g.n[1]);
+  const int c[3] = {x, y, z};
+  T bc[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long gn = i + (long long)(wrap_index(c[a] + 1, g.n[a], g.bc[a]) - c[a]) * g.s[a];
+    bc[a] = T(0.5) * (in.f[5 + a][i] + in.f[5 + a][gn]);
+  }
+  return cell_cmax<T, P64>(in.f[0][i], in.f[1][i], in.f[2][i], in.f[3][i], in.f[4][i], bc[0],
+                           bc[1], bc[2], gamma, st);
+}
+
+// c_max of cells [i0, i1) by one block, folded into ds->cmax
+template <typename T, bool P64>
+__device__ __forceinline__ void cmax_range(const GridDesc& g, const FieldSet<T>& in, T gamma,
+                                           DevScalars* ds, long long i0, long long i1,
+                                           long long stride) {
   T cm = T(0);
   bool nan_seen = false;
   int st = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int z = (int)(i % g.n[2]);
-    const long long xy = i / g.n[2];
-    const int y = (int)(xy % g.n[1]);
-    const int x = (int)(xy / g.n[1]);
-    const int c[3] = {x, y, z};
-    T bc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const long long gn = i + (long long)(wrap_index(c[a] + 1, g.n[a], g.bc[a]) - c[a]) * g.s[a];
-      bc[a] = T(0.5) * (in.f[5 + a][i] + in.f[5 + a][gn]);
-    }
-    const T v = cell_cmax<T, P64>(in.f[0][i], in.f[1][i], in.f[2][i], in.f[3][i], in.f[4][i],
-                                  bc[0], bc[1], bc[2], gamma, &st);
+  for (long long i = i0; i < i1; i += stride) {
+    const T v = cmax_cell<T, P64>(g, in, i, gamma, &st);
     if (v != v) nan_seen = true; else cm = fmax(cm, v);
   }
   block_max_to_global(cm, nan_seen, ds);
   if (st) atomicOr(&ds->status, st);
+}
+
+// c_max of a state (at initialisation, on request, and at the end of a step whose last
+// fluid sweep runs along an axis of one cell)
+template <typename T, bool P64>
+__global__ void cmax_kernel(GridDesc g, FieldSet<T> in, T gamma, DevScalars* ds) {
+  const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+  cmax_range<T, P64>(g, in, gamma, ds, blockIdx.x * (long long)blockDim.x + threadIdx.x, N,
+                     (long long)gridDim.x * blockDim.x);
 }
 
 // dt = cfl h / c_max on the device, clipped to land on t_end (Sect. 4.2 steps 4-5, 8-9)

@@ -1,6 +1,7 @@
 // Launcher bodies shared by the per-precision translation units.
 #pragma once
 
+#include "mhd_flat.cuh"
 #include "mhd_kernels.cuh"
 #include "mhd_launch.h"
 #include "mhd_march.cuh"
@@ -15,7 +16,10 @@ template <typename T>
 static size_t march_smem(int nv) { return sizeof(T) * (size_t)kMarchRing * nv * MarchCfg<T>::NT; }
 // warp segments (z): warps per block, cells per lane
 constexpr int kSegWarps = 4;
-template <typename T> struct SegK { static constexpr int K = 2; };
+#ifndef MHD_SEG_K_F32
+#define MHD_SEG_K_F32 3
+#endif
+template <typename T> struct SegK { static constexpr int K = sizeof(T) == 4 ? MHD_SEG_K_F32 : 2; };
 
 template <typename T, int A, bool LAST, bool P64>
 static cudaError_t set_march_attr() {
@@ -26,6 +30,17 @@ template <typename T, int A>
 static cudaError_t set_ct_march_attr() {
   return cudaFuncSetAttribute(ct_march_xy<T, A, MarchCfg<T>::S, MarchCfg<T>::NT>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem<T>(15));
+}
+// CT with shared EMF rows (ct_rows_xy): warps per block (used where ct_use_rows)
+#ifndef MHD_ROWS_R
+#define MHD_ROWS_R 8
+#endif
+constexpr int kRowsR = MHD_ROWS_R;
+template <typename T, int A>
+static cudaError_t set_ct_rows_attr() {
+  return cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, kRowsR>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ct_rows_smem<T>(kRowsR));
 }
 
 template <typename T, bool P64>
@@ -60,9 +75,15 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
 }
 
 template <typename T>
+static cudaError_t cmax_impl(const GridDesc& g, const FieldSet<T>& in, double gamma,
+                             DevScalars* ds, bool p64, cudaStream_t s);
+
+template <typename T>
 static cudaError_t fluid_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                               double gamma, double h, DevScalars* ds, int axis, bool last,
                               bool p64, cudaStream_t s) {
+  if (axis_is_flat(g, axis))   // identity (mhd_flat.cuh); the caller does not swap buffers
+    return last ? cmax_impl<T>(g, in, gamma, ds, p64, s) : cudaSuccess;
   const T gm = (T)gamma;
   if (last) {
     if (p64) fluid_dispatch<T, true, true>(g, in, out, gm, h, ds, axis, s);
@@ -78,6 +99,25 @@ template <typename T>
 static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                            double h, DevScalars* ds, int axis, cudaStream_t s) {
   constexpr int S = MarchCfg<T>::S, NT = MarchCfg<T>::NT;
+  if (axis_is_flat(g, axis)) {   // B_A only (mhd_flat.cuh); the caller swaps B_A alone
+    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+    long long nb = (N + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    if (axis == 0) ct_flat_kernel<T, 0><<<(unsigned)nb, 256, 0, s>>>(g, in, out, h, ds);
+    else if (axis == 1) ct_flat_kernel<T, 1><<<(unsigned)nb, 256, 0, s>>>(g, in, out, h, ds);
+    else ct_flat_kernel<T, 2><<<(unsigned)nb, 256, 0, s>>>(g, in, out, h, ds);
+    return cudaGetLastError();
+  }
+  if (ct_use_rows(g, axis)) {
+    constexpr int R = kRowsR;
+    const int o = axis == 0 ? 1 : 0;
+    const long long nb = (long long)((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1));
+    const dim3 grid((unsigned)nb, (unsigned)((g.n[axis] + S - 1) / S));
+    const size_t sm = ct_rows_smem<T>(R);
+    if (axis == 0) ct_rows_xy<T, 0, S, R><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
+    else ct_rows_xy<T, 1, S, R><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
+    return cudaGetLastError();
+  }
   if (axis == 0 || axis == 1) {
     const int o = axis == 0 ? 1 : 0;
     const long long np = (long long)g.n[2] * g.n[o];
@@ -122,6 +162,8 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
     if (sizeof(T) == 4) { cudaError_t e2 = setup_p<T, true>(); if (e2 != cudaSuccess) e = e2; } \
     cudaError_t e3 = set_ct_march_attr<T, 0>(); if (e3 != cudaSuccess) e = e3;              \
     e3 = set_ct_march_attr<T, 1>(); if (e3 != cudaSuccess) e = e3;                          \
+    e3 = set_ct_rows_attr<T, 0>(); if (e3 != cudaSuccess) e = e3;                           \
+    e3 = set_ct_rows_attr<T, 1>(); if (e3 != cudaSuccess) e = e3;                           \
     return e;                                                                               \
   }                                                                                         \
   template <> cudaError_t Launch<T>::fluid(const GridDesc& g, const FieldSet<T>& in,        \

@@ -126,6 +126,25 @@ __device__ __forceinline__ void cp_async_wait() {
 constexpr int kMarchDepth = 4;
 constexpr int kMarchRing = kMarchDepth + 1;
 
+// unroll factors of the marching loops: a window of depth d shifts without register moves
+// when the loop body is repeated a multiple of d times
+#ifndef MHD_FLUID_UNROLL
+#define MHD_FLUID_UNROLL 3
+#endif
+#ifndef MHD_CT_UNROLL
+#define MHD_CT_UNROLL 4
+#endif
+// minimum resident blocks per SM requested from the compiler (register cap) for the
+// fluid and CT marches
+#ifndef MHD_MARCH_MINB
+#define MHD_MARCH_MINB 1
+#endif
+#ifndef MHD_CT_MINB
+#define MHD_CT_MINB 4
+#endif
+constexpr int kFluidUnroll = MHD_FLUID_UNROLL;
+constexpr int kCtUnroll = MHD_CT_UNROLL;
+
 // ------------------------------------------------------------------------------------
 // x or y sweep (A = 0, 1): threads take consecutive positions of the transverse plane with
 // z fastest (coalesced rows per field); each thread marches its pencil over S cells plus
@@ -199,6 +218,7 @@ __device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const Fie
   T bn_cur = bn[base + wrap_off<T>(js, nA, bcA, sA)];
   T cm = T(0);
   bool nan_seen = false;
+#pragma unroll kFluidUnroll
   for (int k = 0; k < kend; ++k) {
     issue(k + kMarchDepth);
     cp_async_wait<kMarchDepth>();
@@ -237,7 +257,7 @@ __device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const Fie
 }
 
 template <typename T, int A, bool LAST, bool P64, int S, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, MHD_MARCH_MINB)
 fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   fluid_march_xy_tile<T, A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, blockIdx.x, blockIdx.y,
@@ -406,6 +426,7 @@ __device__ __forceinline__ void ct_march_xy_tile(const GridDesc& g, const FieldS
 #pragma unroll
   for (int d = 0; d < kMarchDepth; ++d) issue(d);
   int st = 0;
+#pragma unroll kCtUnroll
   for (int k = 0; k < kend; ++k) {
     issue(k + kMarchDepth);
     cp_async_wait<kMarchDepth>();
@@ -433,10 +454,138 @@ __device__ __forceinline__ void ct_march_xy_tile(const GridDesc& g, const FieldS
 }
 
 template <typename T, int A, int S, int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, MHD_CT_MINB)
 ct_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ct_march_xy_tile<T, A, S, NT>(g, in, out, h, ds, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// ------------------------------------------------------------------------------------
+// x or y sweep of the constrained transport with every EMF row evaluated once.
+//
+// A block holds R warps; warp w follows transverse row o0 + w of the axis O (the
+// transverse axis that is not z), lane l the pencil z0 + l; both coordinates are wrapped
+// or clamped at the grid's edges like any neighbour index.  Each thread runs the EMF
+// pipelines of its own pencil for t1 and t2.  The constraint on B_A (Algorithm 2) needs, for
+// each transverse axis, the EMF of the row above as well: across z that is lane l+1's
+// (warp shuffle), across O it is warp w+1's (shared memory, one barrier per cell).  So
+// lane 31 and warp R-1 only supply EMFs to their neighbours, and a block updates 31 x (R-1)
+// pencils.  Where the row above is clamped onto the row itself (outflow top edge), the
+// neighbour's pipeline sees the same inputs as the thread's own, which is what the
+// per-thread form (ct_march_xy) computes there too.  Results are identical to ct_march_xy.
+// ------------------------------------------------------------------------------------
+// the shared-row form pays off when a z chunk of 31 pencils and several rows are filled
+constexpr int kRowsMinNz = 48, kRowsMinRows = 4;
+__host__ __device__ inline bool ct_use_rows(const GridDesc& g, int axis) {
+  return axis < 2 && g.n[2] >= kRowsMinNz && g.n[axis == 0 ? 1 : 0] >= kRowsMinRows;
+}
+
+template <typename T, int A, int S, int R>
+__device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSet<T>& in,
+                                                const FieldSet<T>& out, double h, DevScalars* ds,
+                                                unsigned bx, unsigned by,
+                                                unsigned char* smem_raw) {
+  static_assert(A == 0 || A == 1, "x or y sweep");
+  constexpr int O = (A == 0) ? 1 : 0;
+  constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
+  constexpr int NT = 32 * R;
+  constexpr bool Z1 = (T1 == 2);             // the t1 pipeline runs across z (y sweep)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nzc = (g.n[2] + 30) / 31;
+  const int zr = (int)(bx % nzc) * 31 + lane;
+  const int orow = (int)(bx / nzc) * (R - 1) + w;
+  const int zc = wrap_index(zr, g.n[2], g.bc[2]);
+  const int oc = wrap_index(orow, g.n[O], g.bc[O]);
+  const bool out_ok = lane < 31 && zr < g.n[2] && w < R - 1 && orow < g.n[O];
+  const bool halo_row = (w == R - 1);        // supplies the O-row EMF only
+  const int a0 = by * S;
+  const int nA = g.n[A], bcA = g.bc[A];
+  const T dth = (T)(ds->dt / h);
+  const T hd = T(0.5) * dth;
+  const long long base = (long long)zc + (long long)oc * g.s[O];
+  const long long lo_z = (long long)(wrap_index(zc - 1, g.n[2], g.bc[2]) - zc);
+  const long long lo_o = (long long)(wrap_index(oc - 1, g.n[O], g.bc[O]) - oc) * g.s[O];
+  const long long lo1 = Z1 ? lo_z : lo_o, lo2 = Z1 ? lo_o : lo_z;
+  const T* __restrict__ pr = in.f[0];
+  const T* __restrict__ pm = in.f[1 + A];
+  const T* __restrict__ pb1 = in.f[5 + T1];
+  const T* __restrict__ pb2 = in.f[5 + T2];
+  const T* __restrict__ pba = in.f[5 + A];
+  const long long sA = g.s[A];
+  EmfPipe<T> p1, p2;
+  p1.init();
+  p2.init();
+  T ba1 = T(0), ba2 = T(0), ba3 = T(0), ba4 = T(0);
+  const int js = a0 - 4;
+  const int kend = min(S, nA - a0) + 8;
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  T* xbuf = ring + (size_t)kMarchRing * 9 * NT;   // [2][NT] EMF of the O pipeline
+  constexpr int NV = 9;
+  auto issue = [&](int kk) {
+    if (kk < kend) {
+      const long long c = base + (long long)wrap_index(js + kk, nA, bcA) * sA;
+      T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
+      cp_async_elem(slot + 0 * NT, pr + c);
+      cp_async_elem(slot + 1 * NT, pr + c + lo1);
+      cp_async_elem(slot + 2 * NT, pr + c + lo2);
+      cp_async_elem(slot + 3 * NT, pm + c);
+      cp_async_elem(slot + 4 * NT, pm + c + lo1);
+      cp_async_elem(slot + 5 * NT, pm + c + lo2);
+      cp_async_elem(slot + 6 * NT, pb1 + c);
+      cp_async_elem(slot + 7 * NT, pb2 + c);
+      cp_async_elem(slot + 8 * NT, pba + c);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kMarchDepth; ++d) issue(d);
+  int st = 0;
+#pragma unroll kCtUnroll
+  for (int k = 0; k < kend; ++k) {
+    issue(k + kMarchDepth);
+    cp_async_wait<kMarchDepth>();
+    const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+    const int j = js + k;
+    const T r0 = slot[0], r1 = slot[1 * NT], r2 = slot[2 * NT];
+    const T m0 = slot[3 * NT], m1 = slot[4 * NT], m2 = slot[5 * NT];
+    const T vf1 = Num<T>::div(m0 + m1, r0 + r1);     // face velocities below the pencil
+    const T vf2 = Num<T>::div(m0 + m2, r0 + r2);
+    T bt1 = T(0), bt2 = T(0), e1 = T(0), e2 = T(0);
+    // the halo row only feeds the O pipeline's EMF to the row below
+    if (!halo_row || !Z1) bt1 = p1.push(vf1, slot[6 * NT], dth, hd, &e1);
+    if (!halo_row || Z1) bt2 = p2.push(vf2, slot[7 * NT], dth, hd, &e2);
+    const T eo = Z1 ? e2 : e1;                       // EMF of the O pipeline
+    T* xb = xbuf + (k & 1) * NT;
+    xb[threadIdx.x] = eo;
+    __syncthreads();
+    const T eo_up = xb[halo_row ? threadIdx.x : threadIdx.x + 32];
+    const T ez_up = __shfl_down_sync(0xffffffffu, Z1 ? e1 : e2, 1);
+    const T en1 = Z1 ? ez_up : eo_up, en2 = Z1 ? eo_up : ez_up;
+    T b = ba4 + dth * (en1 - e1);            // constraint from t1, then t2
+    b = b + dth * (en2 - e2);
+    ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = slot[8 * NT];
+    if (k >= 8 && out_ok) {
+      const long long co = base + (long long)(j - 4) * sA;
+      out.f[5 + T1][co] = bt1;
+      out.f[5 + T2][co] = bt2;
+      out.f[5 + A][co] = b;
+      if (!(bt1 == bt1) || !(bt2 == bt2) || !(b == b)) st |= ST_NONFINITE;
+    }
+  }
+  cp_async_wait<0>();
+  if (st) atomicOr(&ds->status, st);
+}
+
+template <typename T>
+static size_t ct_rows_smem(int R) {
+  return sizeof(T) * ((size_t)kMarchRing * 9 * 32 * R + 2 * 32 * R);
+}
+
+template <typename T, int A, int S, int R>
+__global__ void __launch_bounds__(32 * R)
+ct_rows_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ct_rows_xy_tile<T, A, S, R>(g, in, out, h, ds, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 }  // namespace mhd

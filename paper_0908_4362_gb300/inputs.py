@@ -415,20 +415,24 @@ class Request:
 
 
 def serving_trace(count: int, rate: float, seed: int = 7, ot_range=(128, 1024),
-                  blast_range=(32, 256), steps_range=(50, 500)) -> list:
+                  blast_range=(32, 256), steps_range=(50, 500), quantum: int = 16) -> list:
     """Poisson arrivals at ``rate`` per second: half Orszag-Tang 2D (square edge
     log-uniform in ot_range), half 3D blast (cubic edge log-uniform in blast_range), each
-    running a step count uniform in steps_range."""
+    running a step count uniform in steps_range.  Edges are rounded to multiples of
+    ``quantum`` (so that requests share initial states).  The requests do not depend on
+    the rate, only their arrival times do (rate 0 or inf: all arrive at time 0)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for i in range(count):
-        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        gap = rng.standard_exponential()            # drawn for every rate: same requests
+        t += gap / rate if 0 < rate < math.inf else 0.0
         if rng.uniform() < 0.5:
             kind, lo, hi = "ot2d", ot_range[0], ot_range[1]
         else:
             kind, lo, hi = "blast3d", blast_range[0], blast_range[1]
         edge = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        edge = max(quantum, int(round(edge / quantum)) * quantum)
         steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
         out.append(Request(i, t, kind, edge, steps))
     return out

@@ -25,8 +25,8 @@ EXPORTS = ("mhd_create", "mhd_init_fields", "mhd_upload", "mhd_step", "mhd_apply
            "mhd_read", "mhd_download", "mhd_sums", "mhd_state", "mhd_set_state", "mhd_sync",
            "mhd_info", "mhd_stream", "mhd_profile", "mhd_profile_read", "mhd_destroy",
            "mhd_status_str", "mhd_last_error", "mhd_sums_noalloc", "mhd_batch_create",
-           "mhd_batch_step", "mhd_batch_sync", "mhd_batch_info", "mhd_batch_destroy",
-           "mhd_batch_selftest_timeout")
+           "mhd_batch_step", "mhd_batch_step_each", "mhd_batch_sync", "mhd_batch_info",
+           "mhd_batch_destroy", "mhd_batch_selftest_timeout")
 
 
 class MhdConfig(C.Structure):
@@ -75,6 +75,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "mhd_sums_noalloc": ([C.POINTER(vp), C.c_int, C.c_longlong, dp, vp], C.c_int),
         "mhd_batch_create": ([C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
         "mhd_batch_step": ([vp, C.c_int], C.c_int),
+        "mhd_batch_step_each": ([vp, ip], C.c_int),
         "mhd_batch_sync": ([vp], C.c_int),
         "mhd_batch_info": ([vp, ip, C.POINTER(C.c_longlong), C.POINTER(vp)], C.c_int),
         "mhd_batch_destroy": ([vp], None),
@@ -272,6 +273,13 @@ class Batch:
         st = self.lib.mhd_batch_step(self.b, int(nsteps))
         if st != MHD_OK:
             raise MhdError(st, f"mhd_batch_step: {self.lib.mhd_status_str(st).decode()}")
+
+    def step_each(self, counts):
+        """Advance solver i by counts[i] steps (0: not at all) in one persistent launch."""
+        arr = (C.c_int * len(self.solvers))(*[int(c) for c in counts])
+        st = self.lib.mhd_batch_step_each(self.b, arr)
+        if st != MHD_OK:
+            raise MhdError(st, f"mhd_batch_step_each: {self.lib.mhd_status_str(st).decode()}")
 
     def sync(self) -> int:
         return self.lib.mhd_batch_sync(self.b)
