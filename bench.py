@@ -48,7 +48,8 @@ STEP_ALG_BYTES = 384
 NCU_TRAFFIC_PER_CELL = {"4ce521d2736026f2": 50.55}
 
 
-KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_launch_impl.cuh")
+KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.cuh",
+                  "mhd_launch_impl.cuh")
 
 
 def kernel_source_hash() -> str:

@@ -317,6 +317,72 @@ struct EmfPipe {
   }
 };
 
+// Packed FP32 arithmetic on float pairs (f32x2 instructions of sm_100+): two independent
+// EMF pipelines advance in one instruction stream, lane x and lane y.
+#ifndef MHD_CT_PACK
+#define MHD_CT_PACK 1
+#endif
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+// lane-wise c > 0 ? a : b
+__device__ __forceinline__ float2 sel_pos2(float2 c, float2 a, float2 b) {
+  return make_float2(c.x > 0.f ? a.x : b.x, c.y > 0.f ? a.y : b.y);
+}
+// lane-wise phi(a, b) / 2 (half_vanleer<float>)
+__device__ __forceinline__ float2 half_vanleer2(float2 a, float2 b) {
+  const float2 ab = mul2(a, b), s = add2(a, b);
+  const float2 q = mul2(ab, make_float2(__fdividef(1.f, s.x), __fdividef(1.f, s.y)));
+  return make_float2(ab.x > 0.f ? q.x : 0.f, ab.y > 0.f ? q.y : 0.f);
+}
+
+// Two EmfPipe<float> in one: lane x and lane y are independent pipelines (same steps).
+struct EmfPipe2 {
+  float2 vf1, vf2, vs1, vs2, vs3, b1, b2, b3, b4, e1p, g3, g4, dp, pp, e2p;
+
+  __device__ __forceinline__ void init() {
+    vf1 = vf2 = vs1 = vs2 = vs3 = b1 = b2 = b3 = b4 = e1p = g3 = g4 = dp = pp = e2p =
+        make_float2(0.f, 0.f);
+  }
+
+  // ndth = -dt/h, nhd = -dt/(2h) in both lanes
+  __device__ __forceinline__ float2 push(float2 vf0, float2 b0, float2 ndth, float2 nhd,
+                                         float2* e2_prev) {
+    const float2 vs0 = mul2(splat2(0.25f), add2(fma2(splat2(2.f), vf1, vf0), vf2));
+    const float2 ve1 = mul2(splat2(0.5f), add2(vs1, vs0));
+    const float2 e1 = sel_pos2(ve1, mul2(vs1, b2), mul2(vs0, b1));
+    const float2 bh = fma2(nhd, sub2(e1, e1p), b2);
+    const float2 g2 = mul2(vs1, bh);
+    const float2 dn = sub2(g2, g3);
+    const float2 pn = half_vanleer2(dp, dn);
+    const float2 ve4 = mul2(splat2(0.5f), add2(vs3, vs2));
+    const float2 e2 = sel_pos2(ve4, add2(g4, pp), sub2(g3, pn));
+    const float2 bt = fma2(ndth, sub2(e2, e2p), b4);
+    *e2_prev = e2p;
+    vf2 = vf1; vf1 = vf0;
+    vs3 = vs2; vs2 = vs1; vs1 = vs0;
+    b4 = b3; b3 = b2; b2 = b1; b1 = b0;
+    e1p = e1;
+    g4 = g3; g3 = g2;
+    dp = dn;
+    pp = pn;
+    e2p = e2;
+    return bt;
+  }
+};
+
 // Offsets of the four cells a thread needs across one transverse axis t: the row itself
 // (own), its lower neighbour (the across-face cell of its EMF row), its upper neighbour
 // (the row whose EMF enters the constraint) and that row's across-face cell, which is
@@ -512,9 +578,13 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
   const T* __restrict__ pb2 = in.f[5 + T2];
   const T* __restrict__ pba = in.f[5 + A];
   const long long sA = g.s[A];
+  constexpr bool PACK = MHD_CT_PACK && sizeof(T) == 4;
   EmfPipe<T> p1, p2;
+  EmfPipe2 pp2;
   p1.init();
   p2.init();
+  pp2.init();
+  const float2 ndth2 = splat2(-(float)dth), nhd2 = splat2(-(float)hd);
   T ba1 = T(0), ba2 = T(0), ba3 = T(0), ba4 = T(0);
   const int js = a0 - 4;
   const int kend = min(S, nA - a0) + 8;
@@ -551,9 +621,17 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
     const T vf1 = Num<T>::div(m0 + m1, r0 + r1);     // face velocities below the pencil
     const T vf2 = Num<T>::div(m0 + m2, r0 + r2);
     T bt1 = T(0), bt2 = T(0), e1 = T(0), e2 = T(0);
-    // the halo row only feeds the O pipeline's EMF to the row below
-    if (!halo_row || !Z1) bt1 = p1.push(vf1, slot[6 * NT], dth, hd, &e1);
-    if (!halo_row || Z1) bt2 = p2.push(vf2, slot[7 * NT], dth, hd, &e2);
+    if constexpr (PACK) {
+      float2 e12;
+      const float2 bt = pp2.push(make_float2((float)vf1, (float)vf2),
+                                 make_float2((float)slot[6 * NT], (float)slot[7 * NT]), ndth2,
+                                 nhd2, &e12);
+      bt1 = bt.x; bt2 = bt.y; e1 = e12.x; e2 = e12.y;
+    } else {
+      // the halo row only feeds the O pipeline's EMF to the row below
+      if (!halo_row || !Z1) bt1 = p1.push(vf1, slot[6 * NT], dth, hd, &e1);
+      if (!halo_row || Z1) bt2 = p2.push(vf2, slot[7 * NT], dth, hd, &e2);
+    }
     const T eo = Z1 ? e2 : e1;                       // EMF of the O pipeline
     T* xb = xbuf + (k & 1) * NT;
     xb[threadIdx.x] = eo;
