@@ -504,6 +504,102 @@ def run_serving(args, world, rank, local):
     return 0
 
 
+def run_vis(args, world, rank, local):
+    """Headless visualization kernels (Sect. 8): frame times of a colour slice of the 512^2
+    Orszag-Tang density and of volume ray casts of the blast pressure at 128^3 and 512^3."""
+    import torch
+
+    from paper_0908_4362_gb300 import build, mhd
+    from paper_0908_4362_gb300 import inputs as I
+
+    build.build()
+    torch.cuda.set_device(local)
+
+    def frames(s, fn, reps=20):
+        st = torch.cuda.ExternalStream(s.stream_handle())
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    with mhd.Solver.from_problem(I.orszag_tang(512), prec=mhd.FP32) as s:
+        s.step(30, sync=True)
+        lo, hi = s.vis_range("rho")
+        res["slice_ot512_ms"] = frames(s, lambda: s.vis_slice("rho", 2, 0, lo, hi))
+    for n in (128, 512):
+        with mhd.Solver.from_problem(I.blast3d(n), prec=mhd.FP32) as s:
+            s.step(10, sync=True)
+            lo, hi = s.vis_range("p")
+            for axis in (0, 2):
+                res[f"volume_blast{n}_axis{axis}_ms"] = frames(
+                    s, lambda: s.vis_volume("p", axis, lo, hi, 0.02), reps=5)
+    if rank == 0:
+        line = {"metric": "frames/s (headless visualization kernels)",
+                "value": 1e3 / res["slice_ot512_ms"], "unit": "frames/s", "n_gpus": world,
+                "steps": None, "warmup": 3, "ms_per_step": res["slice_ot512_ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "colour slice of the 512^2 Orszag-Tang density "
+                                       "(RGBA8); volume ray casts of the 3D blast pressure",
+                           "timing": "CUDA events on the context stream, each call includes "
+                                     "its stream synchronisation"},
+                "frame_ms": res,
+                "note": "the paper's OpenGL frame rates are unavailable on this box (no "
+                        "graphics stack); these are the CUDA kernels producing the same images"}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_precision(args, world, rank, local):
+    """The precision variants on a 256^3 blast: FP32 sweeps, FP32 with the FP64 pressure
+    recovery, and the FP64 parity path (built without FMA contraction).  Their errors
+    against the FP64 oracle are covered by the parity tests."""
+    import numpy as np
+    import torch
+
+    from paper_0908_4362_gb300 import build, mhd
+    from paper_0908_4362_gb300 import inputs as I
+
+    build.build()
+    torch.cuda.set_device(local)
+    n = 256
+    prob = I.blast3d(n, offset=(0.37, -0.21, 0.13))
+    res = {}
+    for name, prec, p64 in (("fp32", mhd.FP32, False), ("fp32_fp64_pressure", mhd.FP32, True),
+                            ("fp64", mhd.FP64, False)):
+        with mhd.Solver(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, prec=prec,
+                        fp64_pressure=p64) as s:
+            s.init_fields(prob.fields)
+            s.step(3, sync=True)
+            st = torch.cuda.ExternalStream(s.stream_handle())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = 10
+            torch.cuda.synchronize()
+            e0.record(st)
+            s.step(k)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            res[name] = {"ms_per_step": ms, "cell_updates_per_s": prob.ncells / (ms / 1e3)}
+    if rank == 0:
+        line = {"metric": "cell-updates/s by precision (256^3 blast)",
+                "value": res["fp64"]["cell_updates_per_s"], "unit": UNIT, "n_gpus": world,
+                "steps": 10, "warmup": 3, "ms_per_step": res["fp64"]["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "3D magnetised blast 256^3 (off-centre), periodic"},
+                "variants": res}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,7 +611,8 @@ def main(argv=None):
     ap.add_argument("--ref-edge", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="blast", choices=["blast", "batched", "serving"])
+    ap.add_argument("--workload", default="blast", choices=["blast", "batched", "serving", "vis",
+                                                      "precision"])
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--requests", type=int, default=500)
     ap.add_argument("--calib", type=int, default=40)
@@ -531,6 +628,10 @@ def main(argv=None):
             return run_batched(args, world, rank, local)
         if args.workload == "serving":
             return run_serving(args, world, rank, local)
+        if args.workload == "vis":
+            return run_vis(args, world, rank, local)
+        if args.workload == "precision":
+            return run_precision(args, world, rank, local)
         return run_ours(args, world, rank, local)
     finally:
         if world > 1:

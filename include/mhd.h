@@ -180,6 +180,43 @@ void mhd_batch_destroy(mhd_batch* b);
  * SM clock cycles (1 .. 4e9) and the call returns MHD_ERR_TIMEOUT; the device stays usable. */
 mhd_status mhd_batch_selftest_timeout(long long spin_cycles);
 
+/* ---------------------------------------------------------------------------------------
+ * Visualization without a graphics API (Sect. 8).  The paper maps the state into OpenGL
+ * buffers (a vertex per cell for 1D problems, a pixel per cell of a 2D problem coloured by a
+ * transfer function, a texture volume render for 3D).  These entry points write the same
+ * products into caller-owned DEVICE buffers on the context's stream and synchronise; no
+ * window or graphics context is involved.  The selected value q of a cell is one of
+ * mhd_quantity, with B averaged from the faces to the cell centre and p = (gamma-1)(E -
+ * |m|^2/(2 rho) - |B|^2/2); arithmetic is in the context's precision.
+ *
+ * Transfer function (the paper does not give one): s = (q - vmin)/(vmax - vmin) clamped to
+ * [0, 1] (NaN to 0) is mapped linearly through five colour stops at s = 0, 1/4, 1/2, 3/4, 1:
+ * (0,0,0.5), (0,0,1), (0,1,1), (1,1,0), (1,0,0).
+ * Errors: MHD_ERR_INVALID for a bad quantity, axis, index, range or NULL pointer;
+ * MHD_ERR_CUDA if a launch fails.
+ * ------------------------------------------------------------------------------------- */
+typedef enum { MHD_Q_RHO = 0, MHD_Q_P = 1, MHD_Q_E = 2, MHD_Q_VMAG = 3, MHD_Q_BMAG = 4 } mhd_quantity;
+
+/* 1D grids (at most one axis longer than 1): xy[2j] = (j + 1/2) h, xy[2j+1] = q(j) for the n
+ * cells of that axis (device pointer, 2n floats) -- the paper's vertex buffer. */
+mhd_status mhd_vis_curve(mhd_ctx* ctx, int quantity, float* xy);
+
+/* The plane of cells normal to `axis` at `index` as an RGBA8 image (device pointer,
+ * w*h*4 bytes, alpha 255): image axes are the two other grid axes u < v, pixel (row v, column
+ * u) at byte 4 (v w + u); each channel is round(255 x colour). */
+mhd_status mhd_vis_slice(mhd_ctx* ctx, int quantity, int axis, int index, double vmin,
+                         double vmax, unsigned char* rgba);
+
+/* Orthographic emission-absorption ray cast along `axis`, one ray per cell column, front to
+ * back (increasing index): with the cell's colour c and opacity a = clamp(opacity x s, 0, 1),
+ * C += (1 - A) a c and A += (1 - A) a.  Output: RGBA float image (device pointer, w*h*4
+ * floats, premultiplied colour and accumulated opacity), pixel layout as mhd_vis_slice. */
+mhd_status mhd_vis_volume(mhd_ctx* ctx, int quantity, int axis, double vmin, double vmax,
+                          double opacity, float* rgba);
+
+/* Minimum and maximum of q over the grid (host outputs), e.g. for vmin/vmax. */
+mhd_status mhd_vis_range(mhd_ctx* ctx, int quantity, double* vmin, double* vmax);
+
 /* FP64 sums of 8 device arrays without allocating device memory.
  *
  * The paper has no counterpart to this entry point.  It exists for callers that cannot

@@ -27,6 +27,7 @@ UNITS = [
     ("mhd_noalloc.cu", []),
     # the batched persistent kernel runs the FP32 sweep bodies: same flags as their TU
     ("mhd_batch.cu", ["--use_fast_math"]),
+    ("mhd_vis.cu", []),
 ]
 
 

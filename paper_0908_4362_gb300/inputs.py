@@ -183,6 +183,61 @@ def orszag_tang(n: int = 512, variant: str = "config", cfl: float = 0.7,
                    f, t_end)
 
 
+def blast2d(n: int = 512, cfl: float = 0.7, t_end: float = 0.2) -> Problem:
+    """2D magnetised blast wave of Sect. 5.2.2 on the periodic unit square, nz = 1: rho = 1,
+    v = 0, B = (1, 1, 0)/sqrt(2), gamma = 5/3, p = 10 inside r < 0.1 about (0.5, 0.5)
+    (cell centres) and 0.1 outside.  The problem's list also prints "p = 5/(12 pi)" on the
+    line with rho and gamma; that value contradicts the inside/outside pressures printed
+    just above it and is read as left over from the Orszag-Tang list."""
+    gamma = 5.0 / 3.0
+    h = 1.0 / n
+    xc = _centres(n, h)
+    r2 = (xc - 0.5)[:, None, None] ** 2 + (xc - 0.5)[None, :, None] ** 2
+    shape = (n, n, 1)
+    p = np.where(r2 < 0.01, 10.0, 0.1) * np.ones(shape)
+    z = np.zeros(shape)
+    b = 1.0 / math.sqrt(2.0)
+    f = conserved(np.ones(shape), [z, z, z], p, [np.full(shape, b), np.full(shape, b), z],
+                  gamma, (PERIODIC,) * 3)
+    return Problem(f"blast2d_{n}", shape, (PERIODIC,) * 3, h, gamma, cfl, f, t_end)
+
+
+def rotor(n: int = 512, variant: int = 1, cfl: float = 0.7) -> Problem:
+    """MHD rotor of Sect. 5.2.3 on the unit square, nz = 1, outflow in x and y.
+
+    A dense disk (rho = 10, r < r0 = 0.1 about (0.5, 0.5)) rotates rigidly at angular
+    speed v0/r0; between r0 and r1 = 0.115 rho = 1 + 9f and the rotation fades with
+    f = (r1 - r)/(r1 - r0); outside rho = 1 and v = 0; p and B = (B0, 0, 0) are uniform.
+    variant 1: v0 = 2, p = 1, gamma = 1.4, B0 = 5/sqrt(4 pi), t_max = 0.15;
+    variant 2: v0 = 1, p = 0.5, gamma = 5/3, B0 = 2.5/sqrt(4 pi), t_max = 0.295.
+    Readings: the taper's v_y is printed as -f v0 (x - 0.5)/r, whose sign would reverse the
+    rotation across r0 (the disk's v_y is +v0 (x - 0.5)/r0); it is read as +f v0 (x-0.5)/r.
+    The boundary type is not stated; outflow (zero gradient) is used."""
+    if variant == 1:
+        v0, p0, gamma, b0, t_end = 2.0, 1.0, 1.4, 5.0 / math.sqrt(4 * math.pi), 0.15
+    elif variant == 2:
+        v0, p0, gamma, b0, t_end = 1.0, 0.5, 5.0 / 3.0, 2.5 / math.sqrt(4 * math.pi), 0.295
+    else:
+        raise ValueError(variant)
+    r0, r1 = 0.1, 0.115
+    h = 1.0 / n
+    xc = _centres(n, h)
+    X = (xc - 0.5)[:, None, None] * np.ones((1, n, 1))
+    Y = (xc - 0.5)[None, :, None] * np.ones((n, 1, 1))
+    r = np.sqrt(X * X + Y * Y)
+    f = (r1 - r) / (r1 - r0)
+    inner, taper = r < r0, (r >= r0) & (r < r1)
+    rho = np.where(inner, 10.0, np.where(taper, 1.0 + 9.0 * f, 1.0))
+    rs = np.where(r > 0, r, 1.0)
+    vx = np.where(inner, -v0 * Y / r0, np.where(taper, -f * v0 * Y / rs, 0.0))
+    vy = np.where(inner, v0 * X / r0, np.where(taper, f * v0 * X / rs, 0.0))
+    shape = (n, n, 1)
+    z = np.zeros(shape)
+    bc = (OUTFLOW, OUTFLOW, PERIODIC)
+    fl = conserved(rho, [vx, vy, z], np.full(shape, p0), [np.full(shape, b0), z, z], gamma, bc)
+    return Problem(f"rotor{variant}_{n}", shape, bc, h, gamma, cfl, fl, t_end)
+
+
 def blast3d(n: int = 512, b_dir=(1.0, 1.0, 0.0), b_mag: float = 1.0, p_in: float = 10.0,
             p_out: float = 0.1, radius: float = 0.1, cfl: float = 0.7,
             shape: tuple | None = None, offset=(0.0, 0.0, 0.0)) -> Problem:

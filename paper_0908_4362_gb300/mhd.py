@@ -26,7 +26,8 @@ EXPORTS = ("mhd_create", "mhd_init_fields", "mhd_upload", "mhd_step", "mhd_apply
            "mhd_info", "mhd_stream", "mhd_profile", "mhd_profile_read", "mhd_destroy",
            "mhd_status_str", "mhd_last_error", "mhd_sums_noalloc", "mhd_batch_create",
            "mhd_batch_step", "mhd_batch_step_each", "mhd_batch_sync", "mhd_batch_info",
-           "mhd_batch_destroy", "mhd_batch_selftest_timeout")
+           "mhd_batch_destroy", "mhd_batch_selftest_timeout", "mhd_vis_curve",
+           "mhd_vis_slice", "mhd_vis_volume", "mhd_vis_range")
 
 
 class MhdConfig(C.Structure):
@@ -76,6 +77,11 @@ def load_library(path: str | None = None) -> C.CDLL:
         "mhd_batch_create": ([C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.POINTER(vp)], C.c_int),
         "mhd_batch_step": ([vp, C.c_int], C.c_int),
         "mhd_batch_step_each": ([vp, ip], C.c_int),
+        "mhd_vis_curve": ([vp, C.c_int, vp], C.c_int),
+        "mhd_vis_slice": ([vp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, vp], C.c_int),
+        "mhd_vis_volume": ([vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, vp],
+                           C.c_int),
+        "mhd_vis_range": ([vp, C.c_int, dp, dp], C.c_int),
         "mhd_batch_sync": ([vp], C.c_int),
         "mhd_batch_info": ([vp, ip, C.POINTER(C.c_longlong), C.POINTER(vp)], C.c_int),
         "mhd_batch_destroy": ([vp], None),
@@ -252,6 +258,58 @@ class Solver:
         s = C.c_void_p()
         self._check(self.lib.mhd_stream(self.ctx, C.byref(s)), "mhd_stream")
         return s.value or 0
+
+    # --- visualization (device buffers from torch; results returned as torch tensors) ---
+    QUANTITIES = {"rho": 0, "p": 1, "E": 2, "vmag": 3, "bmag": 4}
+
+    def _q(self, quantity) -> int:
+        return self.QUANTITIES[quantity] if isinstance(quantity, str) else int(quantity)
+
+    def vis_range(self, quantity="rho"):
+        lo, hi = C.c_double(), C.c_double()
+        self._check(self.lib.mhd_vis_range(self.ctx, self._q(quantity), C.byref(lo),
+                                           C.byref(hi)), "mhd_vis_range")
+        return lo.value, hi.value
+
+    def _image_shape(self, axis: int):
+        if axis not in (0, 1, 2):
+            raise MhdError(MHD_ERR_INVALID, f"axis {axis} is not 0, 1 or 2")
+        u, v = [a for a in range(3) if a != axis]
+        return self.n[v], self.n[u]
+
+    def vis_curve(self, quantity="rho"):
+        import torch
+        n = max(self.n)
+        xy = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        self._check(self.lib.mhd_vis_curve(self.ctx, self._q(quantity), C.c_void_p(xy.data_ptr())),
+                    "mhd_vis_curve")
+        return xy
+
+    def vis_slice(self, quantity="rho", axis=2, index=0, vmin=None, vmax=None):
+        import torch
+        if vmin is None or vmax is None:
+            lo, hi = self.vis_range(quantity)
+            vmin = lo if vmin is None else vmin
+            vmax = (hi if hi > lo else lo + 1.0) if vmax is None else vmax
+        h, w = self._image_shape(axis)
+        img = torch.empty((h, w, 4), dtype=torch.uint8, device="cuda")
+        self._check(self.lib.mhd_vis_slice(self.ctx, self._q(quantity), int(axis), int(index),
+                                           float(vmin), float(vmax),
+                                           C.c_void_p(img.data_ptr())), "mhd_vis_slice")
+        return img
+
+    def vis_volume(self, quantity="rho", axis=2, vmin=None, vmax=None, opacity=0.05):
+        import torch
+        if vmin is None or vmax is None:
+            lo, hi = self.vis_range(quantity)
+            vmin = lo if vmin is None else vmin
+            vmax = (hi if hi > lo else lo + 1.0) if vmax is None else vmax
+        h, w = self._image_shape(axis)
+        img = torch.empty((h, w, 4), dtype=torch.float32, device="cuda")
+        self._check(self.lib.mhd_vis_volume(self.ctx, self._q(quantity), int(axis), float(vmin),
+                                            float(vmax), float(opacity),
+                                            C.c_void_p(img.data_ptr())), "mhd_vis_volume")
+        return img
 
 
 class Batch:

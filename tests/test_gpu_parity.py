@@ -102,6 +102,10 @@ STEP_CASES = [
     ("batched_instance", lambda: I.batched_instance(3)),
     ("zvec_outflow", lambda: I.random_smooth((13, 11, 72), seed=6, bc=(0, 1, 1))),
     ("long_mixed", lambda: I.random_smooth((131, 9, 68), seed=17, bc=(1, 0, 1))),
+    ("dai_woodward_256", lambda: I.dai_woodward(256)),
+    ("blast2d_64", lambda: I.blast2d(64)),
+    ("rotor1_64", lambda: I.rotor(64, 1)),
+    ("rotor2_64", lambda: I.rotor(64, 2)),
 ]
 
 
@@ -127,7 +131,8 @@ def test_ten_steps(mhd, case, prec):
 
 
 BITWISE_CASES = ["blast_40", "random3d_outflow", "orszag_tang_ragged", "brio_wu_512",
-                 "batched_instance", "zvec_outflow", "long_mixed"]
+                 "batched_instance", "zvec_outflow", "long_mixed", "blast2d_64", "rotor1_64",
+                 "dai_woodward_256"]
 
 
 @pytest.mark.parametrize("name", BITWISE_CASES)
@@ -147,6 +152,30 @@ def test_fp32_symmetric_blast_reported(mhd):
     got, ref = run_both(mhd, prob, 10, mhd.FP32)
     err = rel_l1(got, ref.f)
     assert np.all(err <= 2e-3), err
+
+
+SP_DP_CASES = [("rotor1_128", lambda: I.rotor(128, 1)), ("rotor2_128", lambda: I.rotor(128, 2)),
+               ("orszag_tang_128", lambda: I.orszag_tang(128)),
+               ("blast2d_128", lambda: I.blast2d(128))]
+
+
+@pytest.mark.parametrize("case", SP_DP_CASES, ids=[c[0] for c in SP_DP_CASES])
+def test_sp_dp_difference_at_final_time(mhd, case):
+    """FP32 against FP64 on the GPU at the paper's final times (the paper reports the
+    single/double precision differences of its own runs, Sect. 6): both reach t_end, and
+    every field's rel-L1 difference stays small after hundreds of steps with shocks."""
+    prob = case[1]()
+    out = {}
+    for p in (mhd.FP64, mhd.FP32):
+        with mhd.Solver.from_problem(prob, prec=p) as s:
+            n = s.run_to(prob.t_end)
+            t, _, _, _ = s.state()
+            out[p] = (n, t, s.read())
+    (n64, t64, f64), (n32, t32, f32) = out[mhd.FP64], out[mhd.FP32]
+    assert t64 == prob.t_end and t32 == prob.t_end
+    assert abs(n64 - n32) <= max(2, n64 // 100)
+    err = rel_l1(f32, f64)
+    assert np.all(err <= 1e-2), err
 
 
 def test_brio_wu_to_final_time_fp64(mhd):
