@@ -31,7 +31,7 @@
 namespace mhd {
 
 constexpr int kBatchNT = 128;     // threads per CTA (all bodies use 128)
-constexpr int kBatchS = 64;       // march tile length along the sweep
+constexpr int kBatchS = kMarchS;  // march tile length along the sweep (as the single-grid kernels)
 constexpr int kBatchK = 3;        // cells per lane of the z segments
 constexpr long long kSpinCycles = 4000000000LL;   // ~2 s of SM clock per wait
 constexpr int kFlatCells = kBatchNT * 16;   // cells per item of the per-cell operations

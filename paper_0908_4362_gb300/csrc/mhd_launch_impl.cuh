@@ -11,7 +11,7 @@ namespace mhd {
 
 // marching sweeps (x, y): S cells per tile along the sweep, NT pencils per block, shared
 // prefetch ring of kMarchRing iterations x NV values per thread
-template <typename T> struct MarchCfg { static constexpr int S = 64, NT = 128; };
+template <typename T> struct MarchCfg { static constexpr int S = kMarchS, NT = 128; };
 template <typename T>
 static size_t march_smem(int nv) { return sizeof(T) * (size_t)kMarchRing * nv * MarchCfg<T>::NT; }
 // warp segments (z): warps per block, cells per lane

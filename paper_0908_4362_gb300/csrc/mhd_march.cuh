@@ -125,6 +125,13 @@ __device__ __forceinline__ void cp_async_wait() {
 // prefetch depth (iterations ahead) and ring length of the marching kernels
 constexpr int kMarchDepth = 4;
 constexpr int kMarchRing = kMarchDepth + 1;
+// cells per marching tile along the sweep (the halo of 6 or 8 cells is recomputed per
+// tile).  The single-grid kernels and the batched kernel use the same length, so that a
+// grid's FP32 result does not depend on which of them advanced it.
+#ifndef MHD_MARCH_S
+#define MHD_MARCH_S 192
+#endif
+constexpr int kMarchS = MHD_MARCH_S;
 
 // unroll factors of the marching loops: a window of depth d shifts without register moves
 // when the loop body is repeated a multiple of d times
