@@ -456,14 +456,13 @@ mhd_status mhd_cmax(mhd_ctx* ctx, double* cmax) {
   if (!ctx || !cmax) return MHD_ERR_INVALID;
   mhd_status s = sync_scalars(ctx);
   if (s != MHD_OK) return s;
-  const unsigned long long saved = ctx->hs->cmax;
-  unsigned long long zero = 0;
-  CK(cudaMemcpyAsync(&ctx->ds->cmax, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream), "zero");
+  // recompute from the current state: the running maximum is replaced by the same value
+  CK(cudaMemsetAsync(&ctx->ds->cmax, 0, sizeof(ctx->ds->cmax), ctx->stream), "zero");
+  CK(cudaMemsetAsync(ctx->ds->cmax_part, 0, sizeof(ctx->ds->cmax_part), ctx->stream), "zero");
   if ((s = compute_cmax(ctx)) != MHD_OK) return s;
   if ((s = sync_scalars(ctx)) != MHD_OK) return s;
-  *cmax = ctx->esz == 4 ? mhd::Num<float>::from_bits(ctx->hs->cmax)
-                        : mhd::Num<double>::from_bits(ctx->hs->cmax);
-  (void)saved;
+  const unsigned long long bits = mhd::fold_cmax_bits(*ctx->hs);
+  *cmax = ctx->esz == 4 ? mhd::Num<float>::from_bits(bits) : mhd::Num<double>::from_bits(bits);
   return status_from(ctx->status);
 }
 

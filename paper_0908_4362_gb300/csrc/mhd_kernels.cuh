@@ -39,10 +39,23 @@ struct DevScalars {
   double dt;                 // dt of the step in flight (0: step is a no-op)
   double dt_last;            // dt of the last step that advanced t
   double t_end;              // < 0: none
-  unsigned long long cmax;   // bits of the running c_max (float or double), atomicMax
+  unsigned long long cmax;   // bits of the c_max of the current state (float or double)
   int steps_done;            // steps that advanced t
   int status;                // sticky ST_* bits
+  // partial maxima of the running c_max: warps fold their maximum into one of these slots
+  // (atomicMax), spreading what would be one contended address over kCmaxSlots; dt_update
+  // and the host fold them into cmax
+  unsigned long long cmax_part[32];
 };
+constexpr int kCmaxSlots = 32;
+
+// the folded c_max bits: cmax and every partial maximum (non-negative float bits order as
+// unsigned integers)
+__host__ __device__ inline unsigned long long fold_cmax_bits(const DevScalars& s) {
+  unsigned long long m = s.cmax;
+  for (int k = 0; k < kCmaxSlots; ++k) m = s.cmax_part[k] > m ? s.cmax_part[k] : m;
+  return m;
+}
 
 // ------------------------------------------------------------------------------------
 // scalar helpers
@@ -214,7 +227,9 @@ __device__ __forceinline__ void block_max_to_global(T v, bool nan_seen, DevScala
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o));
   bool anynan = __any_sync(mask, nan_seen);
   if ((threadIdx.x & 31) == 0) {
-    if (v > T(0)) atomicMax(&ds->cmax, Num<T>::bits(v));
+    if (v > T(0))
+      atomicMax(&ds->cmax_part[((blockIdx.x << 2) + (threadIdx.x >> 5)) & (kCmaxSlots - 1)],
+                Num<T>::bits(v));
     if (anynan) atomicOr(&ds->status, ST_NONFINITE);
   }
 }
@@ -245,7 +260,7 @@ __device__ __forceinline__ T cmax_cell(const GridDesc& g, const FieldSet<T>& in,
                            bc[1], bc[2], gamma, st);
 }
 
-// c_max of cells [i0, i1) by one block, folded into ds->cmax
+// c_max of cells [i0, i1) by one block, folded into the partial maxima of ds
 template <typename T, bool P64>
 __device__ __forceinline__ void cmax_range(const GridDesc& g, const FieldSet<T>& in, T gamma,
                                            DevScalars* ds, long long i0, long long i1,
@@ -273,7 +288,7 @@ __global__ void cmax_kernel(GridDesc g, FieldSet<T> in, T gamma, DevScalars* ds)
 // dt = cfl h / c_max on the device, clipped to land on t_end (Sect. 4.2 steps 4-5, 8-9)
 template <typename T>
 __device__ __forceinline__ void dt_update(DevScalars* ds, double cfl_h) {
-  const double cm = Num<T>::from_bits(ds->cmax);
+  const double cm = Num<T>::from_bits(fold_cmax_bits(*ds));
   double dt = cfl_h / cm;
   int clipped = 0, active = 1;
   if (!(cm > 0.0) || !(dt == dt) || dt > 1e300) {
@@ -297,6 +312,7 @@ __device__ __forceinline__ void dt_update(DevScalars* ds, double cfl_h) {
     ds->steps_done += 1;
   }
   ds->cmax = 0ull;   // the last sweep of this step accumulates the next c_max
+  for (int k = 0; k < kCmaxSlots; ++k) ds->cmax_part[k] = 0ull;
 }
 
 template <typename T>
