@@ -45,7 +45,7 @@ STEP_ALG_BYTES = 384
 # DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
 # a step) from ncu captures on a 256^3 grid (profiles/sweep_kernels_blast256_fp32.md), keyed
 # by the hash of the kernel sources they were taken on; another hash reports null.
-NCU_TRAFFIC_PER_CELL = {"799718804497dbbf": 50.58}
+NCU_TRAFFIC_PER_CELL = {"750bdfbd8cad78b7": 50.62}
 
 
 KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.cuh",
@@ -440,6 +440,7 @@ def run_serving(args, world, rank, local):
     launches.  Three passes: saturation (a prefix of the trace, all requests at time 0:
     capacity of each form), then the whole trace with Poisson arrivals at `load` x the
     served capacity, through both forms (p50/p99 time to result)."""
+    import numpy as np
     import torch
 
     from paper_0908_4362_gb300 import build, serve
@@ -447,7 +448,7 @@ def run_serving(args, world, rank, local):
 
     build.build()
     torch.cuda.set_device(local)
-    digest = (lambda a: hashlib.sha1(a.tobytes()).hexdigest())
+    digest = (lambda a: hashlib.sha1(np.ascontiguousarray(a)).hexdigest())
     be = serve.GpuBackend()
     ics = serve.ICCache(pinned=True)
     base = I.serving_trace(args.requests, 0.0, seed=7 + rank)

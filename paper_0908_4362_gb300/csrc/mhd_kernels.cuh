@@ -45,9 +45,9 @@ struct DevScalars {
   // partial maxima of the running c_max: warps fold their maximum into one of these slots
   // (atomicMax), spreading what would be one contended address over kCmaxSlots; dt_update
   // and the host fold them into cmax
-  unsigned long long cmax_part[32];
+  unsigned long long cmax_part[128];
 };
-constexpr int kCmaxSlots = 32;
+constexpr int kCmaxSlots = 128;
 
 // the folded c_max bits: cmax and every partial maximum (non-negative float bits order as
 // unsigned integers)

@@ -5,15 +5,16 @@ admits them in arrival order while their device memory fits a budget, keeps ever
 state resident in HBM, and advances all active requests together: each iteration is one
 persistent batched launch (mhd_batch_step_each) in which request i advances by its own
 step count s_i; grids large enough to fill the GPU by themselves run their s_i steps as
-plain graph launches on their own streams, concurrently with that launch.  The counts give
-every active request about the same number of cell updates per iteration, sized so that an
-iteration takes about `iter_ms` at the measured throughput: a small grid takes many steps
-per iteration and finishes soon, a large one takes a few (processor sharing by work).  Counts of 3 or more are multiples of 3, so that
-the axis-order phase of every request is the same from one iteration to the next and the
-launch's work list and graph are reused.  Requests that finish are read back and leave,
-freeing memory for the next arrivals, which join at the next iteration.  Each request's
-result is the same bits as running it alone (the batched launch runs the same arithmetic
-per grid).
+plain graph launches on their own streams, concurrently with that launch.  The counts share
+the cell updates of an iteration (sized so that it takes about `iter_ms` at the measured
+throughput) among the active requests, with weights that grow with each request's waiting
+time: a small grid takes many steps per iteration and finishes soon, a large one a few, and
+long-waiting requests get more.  Counts of 3 or more are multiples of 3, so that the
+axis-order phase of every request is the same from one iteration to the next and the
+launch's work list and graph are reused.  Requests that finish leave the batch and are read
+back while the next iteration runs, freeing memory for the next arrivals, which join at the
+next iteration.  Each request's result is the same bits as running it alone (the batched
+launch runs the same arithmetic per grid).
 
 The scheduling logic talks to the GPU through a small backend interface (`GpuBackend`),
 so that it can be exercised with a fake backend on a machine without a GPU.
@@ -66,9 +67,15 @@ class GpuBackend:
         handle.step(n)
 
     def read(self, handle) -> np.ndarray:
-        out = [np.empty(handle.ncells, dtype=np.float32) for _ in range(8)]
-        handle.download(out)
-        return np.stack(out)
+        """The 8 FP32 fields, (8, N), downloaded into a reused page-locked buffer: the
+        returned array is valid until the next read."""
+        import torch
+        n = 8 * handle.ncells
+        if getattr(self, "_pin", None) is None or self._pin.numel() < n:
+            self._pin = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        views = [self._pin[k * handle.ncells:(k + 1) * handle.ncells] for k in range(8)]
+        handle.download(views)
+        return self._pin[:n].numpy().reshape(8, handle.ncells)
 
     def sync(self, batch):
         st = batch.sync()
@@ -159,18 +166,20 @@ class Server:
         """Serve the requests of `trace` (arrival times in seconds from now); returns the
         jobs with their admission and completion times.
 
-        Each iteration launches the active set, then admits the requests that arrived
-        meanwhile (creating and uploading their states while the GPU works), waits for the
-        launch, and retires the requests that finished.  A request admitted during an
-        iteration joins the next one."""
+        Each iteration launches the active set, then, while the GPU works, admits the
+        requests that arrived (creating and uploading their states) and reads back the
+        requests that finished in the previous iteration; then it waits for the launch.  A
+        request admitted during an iteration joins the next one; a request is complete
+        when its result has been read back."""
         pending = collections.deque(sorted(trace, key=lambda r: r.arrival))
         jobs: list = []
         active: list = []
+        to_retire: list = []
         self._used = 0
         batch, batch_ids = None, None
         tm = self.times
         t0 = self.clock()
-        while pending or active:
+        while pending or active or to_retire:
             counts = []
             big = [j for j in active if j.req.ncells >= self.plain_min_cells]
             small = [j for j in active if j.req.ncells < self.plain_min_cells]
@@ -197,6 +206,20 @@ class Server:
             a0 = self.clock()
             newly = self._admit(pending, jobs, t0)
             tm["admit"] += self.clock() - a0
+            # read back what finished in the previous iteration (overlaps the launch)
+            if to_retire:
+                r0 = self.clock()
+                for j in to_retire:
+                    res = self.be.read(j.handle)
+                    j.done = self.clock() - t0
+                    if self.keep_results:
+                        j.result = (self.keep_results(res) if callable(self.keep_results)
+                                    else np.array(res))
+                    self.be.close(j.handle)
+                    j.handle = None
+                    self._used -= j.need
+                to_retire = []
+                tm["retire"] += self.clock() - r0
             if not active:
                 if not newly and pending:
                     wait = pending[0].arrival - (self.clock() - t0)
@@ -219,22 +242,14 @@ class Server:
             dt = w1 - c0
             if dt > 0 and work > 0:
                 self.rate = 0.7 * self.rate + 0.3 * (work / dt)
-            # retire finished requests (the batch never outlives its contexts)
+            # finished requests leave the batch now (it never outlives its contexts) and are
+            # read back during the next iteration
             finished = [j for j in active if j.remaining == 0]
             if finished:
-                r0 = self.clock()
                 if batch is not None and any(j.remaining == 0 for j in small):
                     batch.close()
                     batch, batch_ids = None, None
-                for j in finished:
-                    res = self.be.read(j.handle)
-                    j.done = self.clock() - t0
-                    if self.keep_results:
-                        j.result = self.keep_results(res) if callable(self.keep_results) else res
-                    self.be.close(j.handle)
-                    j.handle = None
-                    self._used -= j.need
-                tm["retire"] += self.clock() - r0
+                to_retire = finished
             active = [j for j in active if j.remaining > 0] + newly
         if batch is not None:
             batch.close()
@@ -279,7 +294,7 @@ def serve_sequential(backend, trace, ics: ICCache | None = None, clock=time.perf
         res = backend.read(job.handle)
         job.done = clock() - t0
         if keep_results:
-            job.result = keep_results(res) if callable(keep_results) else res
+            job.result = keep_results(res) if callable(keep_results) else np.array(res)
         backend.close(job.handle)
         job.handle = None
         job.remaining = 0
