@@ -547,6 +547,11 @@ ct_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* d
 // neighbour's pipeline sees the same inputs as the thread's own, which is what the
 // per-thread form (ct_march_xy) computes there too.  Results are identical to ct_march_xy.
 // ------------------------------------------------------------------------------------
+// the EMF exchange of the shared-row CT synchronises row pairs with named barriers instead
+// of the whole block (1), or uses the block barrier (0)
+#ifndef MHD_CT_PAIR_BARRIERS
+#define MHD_CT_PAIR_BARRIERS 1
+#endif
 // the shared-row form pays off when a z chunk of 31 pencils and several rows are filled
 constexpr int kRowsMinNz = 48, kRowsMinRows = 4;
 __host__ __device__ inline bool ct_use_rows(const GridDesc& g, int axis) {
@@ -642,7 +647,14 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
     const T eo = Z1 ? e2 : e1;                       // EMF of the O pipeline
     T* xb = xbuf + (k & 1) * NT;
     xb[threadIdx.x] = eo;
+#if MHD_CT_PAIR_BARRIERS
+    // warp w hands its value to warp w-1 (barrier w) and takes warp w+1's (barrier w+1):
+    // each named barrier joins just the two warps of one row pair (64 threads)
+    if (w > 0) asm volatile("bar.sync %0, 64;" ::"r"(w) : "memory");
+    if (w < R - 1) asm volatile("bar.sync %0, 64;" ::"r"(w + 1) : "memory");
+#else
     __syncthreads();
+#endif
     const T eo_up = xb[halo_row ? threadIdx.x : threadIdx.x + 32];
     const T ez_up = __shfl_down_sync(0xffffffffu, Z1 ? e1 : e2, 1);
     const T en1 = Z1 ? ez_up : eo_up, en2 = Z1 ? eo_up : ez_up;
