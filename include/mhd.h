@@ -144,7 +144,8 @@ typedef struct mhd_batch mhd_batch;
 
 /* Create a batch over n contexts (FP32, fp64_pressure off, no t_end pending).  The
  * contexts must outlive the batch.  z_tile_warps: warp segments per work item of a z sweep
- * (0: chosen per sweep, about 1024 items, 4 to 128 segments each); ctas_per_sm: resident CTAs per SM of the persistent launch (0: as many as fit).
+ * (0: chosen per sweep, about 1024 items, 4 to 128 segments each); ctas_per_sm: resident
+ * CTAs per SM of the persistent launch (0: as many as fit).
  * Both are launch shapes only (results do not depend on them); the autotuner picks them. */
 mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int ctas_per_sm,
                             mhd_batch** out);
