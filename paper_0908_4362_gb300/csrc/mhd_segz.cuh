@@ -203,6 +203,58 @@ __device__ __forceinline__ void emf_seg(const T (&vf)[K], T (&bt)[K], T dth, T h
   for (int i = 0; i < K; ++i) bt[i] = bt[i] - dth * (e2[i] - e2m[i]);
 }
 
+// emf_seg<float> of two pipelines at once (lane x and lane y of each float2), f32x2
+// arithmetic; the neighbour values come through two shuffles per shift as before
+template <int K>
+__device__ __forceinline__ void next_cell2(const float2 (&x)[K], float2 (&xn)[K]) {
+  const float2 from_next_lane = make_float2(shdown(x[0].x), shdown(x[0].y));
+#pragma unroll
+  for (int i = 0; i < K; ++i) xn[i] = (i + 1 < K) ? x[i + 1] : from_next_lane;
+}
+template <int K>
+__device__ __forceinline__ void prev_cell2(const float2 (&x)[K], float2 (&xp)[K]) {
+  const float2 from_prev_lane = make_float2(shup(x[K - 1].x), shup(x[K - 1].y));
+#pragma unroll
+  for (int i = 0; i < K; ++i) xp[i] = (i > 0) ? x[i - 1] : from_prev_lane;
+}
+template <int K>
+__device__ __forceinline__ void emf_seg2(const float2 (&vf)[K], float2 (&bt)[K], float2 ndth,
+                                         float2 nhd, float2 (&e2m)[K]) {
+  float2 vn[K], vp[K], vs[K], vsn[K], f[K], fn[K], e1[K], e1p[K], gg[K], ggn[K], d[K], dp[K],
+      P[K], Pn[K], ve[K];
+  next_cell2<K>(vf, vn);
+  prev_cell2<K>(vf, vp);
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    vs[i] = mul2(splat2(0.25f), add2(fma2(splat2(2.f), vf[i], vn[i]), vp[i]));
+  next_cell2<K>(vs, vsn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) f[i] = mul2(vs[i], bt[i]);
+  next_cell2<K>(f, fn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    ve[i] = mul2(splat2(0.5f), add2(vs[i], vsn[i]));            // edge velocity at +1/2
+    e1[i] = sel_pos2(ve[i], f[i], fn[i]);                        // first-order EMF
+  }
+  prev_cell2<K>(e1, e1p);
+#pragma unroll
+  for (int i = 0; i < K; ++i) gg[i] = mul2(vs[i], fma2(nhd, sub2(e1[i], e1p[i]), bt[i]));
+  next_cell2<K>(gg, ggn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) d[i] = sub2(ggn[i], gg[i]);
+  prev_cell2<K>(d, dp);
+#pragma unroll
+  for (int i = 0; i < K; ++i) P[i] = half_vanleer2(dp[i], d[i]);
+  next_cell2<K>(P, Pn);
+  float2 e2[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    e2[i] = sel_pos2(ve[i], add2(gg[i], P[i]), sub2(ggn[i], Pn[i]));   // limited EMF at +1/2
+  prev_cell2<K>(e2, e2m);
+#pragma unroll
+  for (int i = 0; i < K; ++i) bt[i] = fma2(ndth, sub2(e2[i], e2m[i]), bt[i]);
+}
+
 template <typename T, int K, bool NC>
 __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                               const FieldSet<T>& out, double h, DevScalars* ds,
@@ -250,10 +302,31 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
                              : Num<T>::div(m[4] + m[0], r[4] + r[0]);
   }
   T eo1[K], en1[K], eo2[K], en2[K];
-  emf_seg<T, K>(vo1, b1o, dth, hd, eo1);
-  emf_seg<T, K>(vn1, b1h, dth, hd, en1);
-  emf_seg<T, K>(vo2, b2o, dth, hd, eo2);
-  emf_seg<T, K>(vn2, b2h, dth, hd, en2);
+  if constexpr (sizeof(T) == 4 && MHD_CT_PACK) {
+    // the own-row pipelines of t1 and t2 as one packed pair, the upper-row ones as another
+    float2 vo[K], vn[K], bo[K], bh[K], eo[K], en[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      vo[i] = make_float2(vo1[i], vo2[i]);
+      vn[i] = make_float2(vn1[i], vn2[i]);
+      bo[i] = make_float2(b1o[i], b2o[i]);
+      bh[i] = make_float2(b1h[i], b2h[i]);
+    }
+    const float2 ndth2 = splat2(-(float)dth), nhd2 = splat2(-(float)hd);
+    emf_seg2<K>(vo, bo, ndth2, nhd2, eo);
+    emf_seg2<K>(vn, bh, ndth2, nhd2, en);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      b1o[i] = bo[i].x; b2o[i] = bo[i].y;
+      eo1[i] = eo[i].x; eo2[i] = eo[i].y;
+      en1[i] = en[i].x; en2[i] = en[i].y;
+    }
+  } else {
+    emf_seg<T, K>(vo1, b1o, dth, hd, eo1);
+    emf_seg<T, K>(vn1, b1h, dth, hd, en1);
+    emf_seg<T, K>(vo2, b2o, dth, hd, eo2);
+    emf_seg<T, K>(vn2, b2h, dth, hd, en2);
+  }
   int st = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
