@@ -40,6 +40,70 @@ __device__ __forceinline__ void prev_cell(const T (&x)[K], T (&xp)[K]) {
   for (int i = 0; i < K; ++i) xp[i] = (i > 0) ? x[i - 1] : from_prev_lane;
 }
 
+// next/previous cell of packed pairs: two shuffles per shift
+template <int K>
+__device__ __forceinline__ void next_cell2(const float2 (&x)[K], float2 (&xn)[K]) {
+  const float2 from_next_lane = make_float2(shdown(x[0].x), shdown(x[0].y));
+#pragma unroll
+  for (int i = 0; i < K; ++i) xn[i] = (i + 1 < K) ? x[i + 1] : from_next_lane;
+}
+template <int K>
+__device__ __forceinline__ void prev_cell2(const float2 (&x)[K], float2 (&xp)[K]) {
+  const float2 from_prev_lane = make_float2(shup(x[K - 1].x), shup(x[K - 1].y));
+#pragma unroll
+  for (int i = 0; i < K; ++i) xp[i] = (i > 0) ? x[i - 1] : from_prev_lane;
+}
+// Component loops of the fluid segments (packing component pairs into f32x2 was measured
+// slower here: 1.91 -> 2.02 ms at 512^3, the pair moves and the lower occupancy cost more
+// than the halved arithmetic).
+template <typename T> struct Vec {
+  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T fnma(T s, T a, T b) { return b - s * a; }   // b - s a
+  static __device__ __forceinline__ T hv(T a, T b) { return half_vanleer(a, b); }
+  static __device__ __forceinline__ T splat(T v) { return v; }
+  template <int K>
+  static __device__ __forceinline__ void next(const T (&x)[K], T (&xn)[K]) { next_cell<T, K>(x, xn); }
+  template <int K>
+  static __device__ __forceinline__ void prev(const T (&x)[K], T (&xp)[K]) { prev_cell<T, K>(x, xp); }
+};
+// stage 1 of one component: first-order fluxes and the half step
+template <typename V, int K>
+__device__ __forceinline__ void seg_stage1(const V (&fr)[K], const V (&fl)[K], const V (&u)[K],
+                                           V hd, V (&uh)[K]) {
+  V fln[K], g1[K], g1p[K];
+  Vec<V>::template next<K>(fl, fln);
+#pragma unroll
+  for (int i = 0; i < K; ++i) g1[i] = Vec<V>::sub(fr[i], fln[i]);   // first-order flux at +1/2
+  Vec<V>::template prev<K>(g1, g1p);
+#pragma unroll
+  for (int i = 0; i < K; ++i) uh[i] = Vec<V>::fnma(hd, Vec<V>::sub(g1[i], g1p[i]), u[i]);
+}
+
+// stage 2 of one component: limited fluxes and the full update
+template <typename V, int K>
+__device__ __forceinline__ void seg_stage2(const V (&fr2)[K], const V (&fl2)[K], const V (&u)[K],
+                                           V dth, V (&un)[K]) {
+  V frn[K], dR[K], dRp[K], fln[K], dL[K], dLn[K], g2[K], g2p[K];
+  Vec<V>::template next<K>(fr2, frn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) dR[i] = Vec<V>::sub(frn[i], fr2[i]);   // FR2(w+1) - FR2(w)
+  Vec<V>::template prev<K>(dR, dRp);
+  Vec<V>::template next<K>(fl2, fln);
+#pragma unroll
+  for (int i = 0; i < K; ++i) dL[i] = Vec<V>::sub(fln[i], fl2[i]);   // FL2(w+1) - FL2(w)
+  Vec<V>::template next<K>(dL, dLn);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const V right = Vec<V>::add(fr2[i], Vec<V>::hv(dRp[i], dR[i]));
+    const V left = Vec<V>::sub(fln[i], Vec<V>::hv(dL[i], dLn[i]));
+    g2[i] = Vec<V>::sub(right, left);                                // limited flux at +1/2
+  }
+  Vec<V>::template prev<K>(g2, g2p);
+#pragma unroll
+  for (int i = 0; i < K; ++i) un[i] = Vec<V>::fnma(dth, Vec<V>::sub(g2[i], g2p[i]), u[i]);
+}
+
 // one warp: segment `wid` (pencil wid / nseg, segment wid % nseg); all 32 lanes call it
 template <typename T, bool LAST, bool P64, int K, bool NC>
 __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
@@ -87,16 +151,17 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
 #pragma unroll
       for (int q = 0; q < 5; ++q) { fr[q][i] = a[q]; fl[q][i] = c[q]; }
     }
+    T uq[5][K], uhq[5][K];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      T fln[K], g1[K], g1p[K];
-      next_cell<T, K>(fl[q], fln);
+    for (int q = 0; q < 5; ++q)
 #pragma unroll
-      for (int i = 0; i < K; ++i) g1[i] = fr[q][i] - fln[i];       // first-order flux at +1/2
-      prev_cell<T, K>(g1, g1p);
+      for (int i = 0; i < K; ++i) uq[q][i] = u[i][q];
 #pragma unroll
-      for (int i = 0; i < K; ++i) uh[i][q] = u[i][q] - hd * (g1[i] - g1p[i]);
-    }
+    for (int q = 0; q < 5; ++q) seg_stage1<T, K>(fr[q], fl[q], uq[q], hd, uhq[q]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int i = 0; i < K; ++i) uh[i][q] = uhq[q][i];
   }
   // stage 2: limited fluxes of u^{t+dt/2}, full update
   T un[K][5];
@@ -111,27 +176,17 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
 #pragma unroll
       for (int q = 0; q < 5; ++q) { fr2[q][i] = a[q]; fl2[q][i] = c[q]; }
     }
+    T uq[5][K], unq[5][K];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      T frn[K], dR[K], dRp[K], fln[K], dL[K], dLn[K], g2[K], g2p[K];
-      next_cell<T, K>(fr2[q], frn);
+    for (int q = 0; q < 5; ++q)
 #pragma unroll
-      for (int i = 0; i < K; ++i) dR[i] = frn[i] - fr2[q][i];      // FR2(w+1) - FR2(w)
-      prev_cell<T, K>(dR, dRp);
-      next_cell<T, K>(fl2[q], fln);
+      for (int i = 0; i < K; ++i) uq[q][i] = u[i][q];
 #pragma unroll
-      for (int i = 0; i < K; ++i) dL[i] = fln[i] - fl2[q][i];      // FL2(w+1) - FL2(w)
-      next_cell<T, K>(dL, dLn);
+    for (int q = 0; q < 5; ++q) seg_stage2<T, K>(fr2[q], fl2[q], uq[q], dth, unq[q]);
 #pragma unroll
-      for (int i = 0; i < K; ++i) {
-        const T right = fr2[q][i] + half_vanleer(dRp[i], dR[i]);
-        const T left = fln[i] - half_vanleer(dL[i], dLn[i]);
-        g2[i] = right - left;                                      // limited flux at +1/2
-      }
-      prev_cell<T, K>(g2, g2p);
+    for (int q = 0; q < 5; ++q)
 #pragma unroll
-      for (int i = 0; i < K; ++i) un[i][q] = u[i][q] - dth * (g2[i] - g2p[i]);
-    }
+      for (int i = 0; i < K; ++i) un[i][q] = unq[q][i];
   }
   T cm = T(0);
   bool nan_seen = false;
@@ -204,19 +259,7 @@ __device__ __forceinline__ void emf_seg(const T (&vf)[K], T (&bt)[K], T dth, T h
 }
 
 // emf_seg<float> of two pipelines at once (lane x and lane y of each float2), f32x2
-// arithmetic; the neighbour values come through two shuffles per shift as before
-template <int K>
-__device__ __forceinline__ void next_cell2(const float2 (&x)[K], float2 (&xn)[K]) {
-  const float2 from_next_lane = make_float2(shdown(x[0].x), shdown(x[0].y));
-#pragma unroll
-  for (int i = 0; i < K; ++i) xn[i] = (i + 1 < K) ? x[i + 1] : from_next_lane;
-}
-template <int K>
-__device__ __forceinline__ void prev_cell2(const float2 (&x)[K], float2 (&xp)[K]) {
-  const float2 from_prev_lane = make_float2(shup(x[K - 1].x), shup(x[K - 1].y));
-#pragma unroll
-  for (int i = 0; i < K; ++i) xp[i] = (i > 0) ? x[i - 1] : from_prev_lane;
-}
+// arithmetic
 template <int K>
 __device__ __forceinline__ void emf_seg2(const float2 (&vf)[K], float2 (&bt)[K], float2 ndth,
                                          float2 nhd, float2 (&e2m)[K]) {
