@@ -412,11 +412,14 @@ __device__ __forceinline__ TransverseOffsets transverse_offsets(int c, int n, in
 
 template <typename T>
 struct CtColumn {
+  static constexpr bool PACK = MHD_CT_PACK && sizeof(T) == 4;
   EmfPipe<T> own1, nb1, own2, nb2;
+  EmfPipe2 ownp, nbp;     // FP32: (own1, own2) and (nb1, nb2) as packed pairs
   T ba1, ba2, ba3, ba4;   // B_A(j-1..j-4)
 
   __device__ __forceinline__ void init() {
     own1.init(); nb1.init(); own2.init(); nb2.init();
+    ownp.init(); nbp.init();
     ba1 = ba2 = ba3 = ba4 = T(0);
   }
 
@@ -430,10 +433,21 @@ struct CtColumn {
     const T vo2 = Num<T>::div(m[0] + m[3], r[0] + r[3]);
     const T vn2 = hx2 ? Num<T>::div(m[4] + m[3], r[4] + r[3]) : Num<T>::div(m[4] + m[0], r[4] + r[0]);
     T eo1, en1, eo2, en2;
-    *bt1 = own1.push(vo1, b1o, dth, hd, &eo1);
-    nb1.push(vn1, b1h, dth, hd, &en1);
-    *bt2 = own2.push(vo2, b2o, dth, hd, &eo2);
-    nb2.push(vn2, b2h, dth, hd, &en2);
+    if constexpr (PACK) {
+      const float2 ndth = splat2(-(float)dth), nhd = splat2(-(float)hd);
+      float2 eo, en;
+      const float2 bt = ownp.push(make_float2((float)vo1, (float)vo2),
+                                  make_float2((float)b1o, (float)b2o), ndth, nhd, &eo);
+      nbp.push(make_float2((float)vn1, (float)vn2), make_float2((float)b1h, (float)b2h), ndth,
+               nhd, &en);
+      *bt1 = bt.x; *bt2 = bt.y;
+      eo1 = eo.x; eo2 = eo.y; en1 = en.x; en2 = en.y;
+    } else {
+      *bt1 = own1.push(vo1, b1o, dth, hd, &eo1);
+      nb1.push(vn1, b1h, dth, hd, &en1);
+      *bt2 = own2.push(vo2, b2o, dth, hd, &eo2);
+      nb2.push(vn2, b2h, dth, hd, &en2);
+    }
     T b = ba4 + dth * (en1 - eo1);           // constraint from t1, then t2
     b = b + dth * (en2 - eo2);
     *bA = b;
