@@ -32,7 +32,7 @@ namespace mhd {
 
 constexpr int kBatchNT = 128;     // threads per CTA (all bodies use 128)
 constexpr int kBatchS = kMarchS;  // march tile length along the sweep (as the single-grid kernels)
-constexpr int kBatchK = 3;        // cells per lane of the z segments
+constexpr int kBatchK = 3;        // cells per lane of the z segments (or 2, seg_k_for)
 constexpr long long kSpinCycles = 4000000000LL;   // ~2 s of SM clock per wait
 constexpr int kFlatCells = kBatchNT * 16;   // cells per item of the per-cell operations
 constexpr long long kAutoTiles = 1024;      // target items per z sweep when not set
@@ -47,6 +47,7 @@ struct BatchOp {
   GridDesc g;
   int kind, axis, last;
   int rows;            // CT x/y in the shared-row form (ct_rows_xy_tile)
+  int segk;            // z segments: cells per lane (2 or 3, seg_k_for)
   int gx;              // march: tiles across the transverse plane (tile = by * gx + bx)
   int wpt;             // z segments: warp segments per tile
   long long nwarps;    // z segments: warp segments of the sweep
@@ -179,15 +180,28 @@ __global__ void __launch_bounds__(kBatchNT, MHD_BATCH_MINB) batch_kernel(BatchAr
       const long long w0 = (long long)it.tile * op.wpt;
       const long long w1 = min(w0 + op.wpt, op.nwarps);
       for (long long w = w0 + warp; w < w1; w += kBatchNT / 32) {
-        if (op.kind == OP_FLUID) {
-          if (op.last)
-            fluid_seg_z_warp<float, true, false, kBatchK, false>(op.g, op.in, op.out, ins.gamma,
-                                                                 ins.h, ins.ds, w);
-          else
-            fluid_seg_z_warp<float, false, false, kBatchK, false>(op.g, op.in, op.out, ins.gamma,
-                                                                  ins.h, ins.ds, w);
+        if (op.segk == 2) {
+          if (op.kind == OP_FLUID) {
+            if (op.last)
+              fluid_seg_z_warp<float, true, false, 2, false>(op.g, op.in, op.out, ins.gamma, ins.h,
+                                                             ins.ds, w);
+            else
+              fluid_seg_z_warp<float, false, false, 2, false>(op.g, op.in, op.out, ins.gamma,
+                                                              ins.h, ins.ds, w);
+          } else {
+            ct_seg_z_warp<float, 2, false>(op.g, op.in, op.out, ins.h, ins.ds, w);
+          }
         } else {
-          ct_seg_z_warp<float, kBatchK, false>(op.g, op.in, op.out, ins.h, ins.ds, w);
+          if (op.kind == OP_FLUID) {
+            if (op.last)
+              fluid_seg_z_warp<float, true, false, kBatchK, false>(op.g, op.in, op.out, ins.gamma,
+                                                                   ins.h, ins.ds, w);
+            else
+              fluid_seg_z_warp<float, false, false, kBatchK, false>(op.g, op.in, op.out,
+                                                                    ins.gamma, ins.h, ins.ds, w);
+          } else {
+            ct_seg_z_warp<float, kBatchK, false>(op.g, op.in, op.out, ins.h, ins.ds, w);
+          }
         }
       }
     }
@@ -268,7 +282,8 @@ static void build_step_ops(const mhd_ctx* c, int phase, int wpt, BatchOp* out) {
                       : (int)((np + mhd::kBatchNT - 1) / mhd::kBatchNT);
       op.tiles = op.gx * ((g.n[op.axis] + mhd::kBatchS - 1) / mhd::kBatchS);
     } else {
-      const int seg = 32 * mhd::kBatchK - (op.kind == mhd::OP_FLUID ? 6 : 8);
+      op.segk = mhd::seg_k_for(g.n[2]);
+      const int seg = 32 * op.segk - (op.kind == mhd::OP_FLUID ? 6 : 8);
       op.nwarps = (long long)g.n[0] * g.n[1] * ((g.n[2] + seg - 1) / seg);
       // 0: about kAutoTiles items per z sweep (small grids get short items, large ones
       // up to 128 warp segments each)

@@ -68,6 +68,13 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
     else fluid_march_xy<T, 1, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
     return;
   }
+  if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
+    constexpr int K = 2, SEG = 32 * K - 6;
+    const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
+    fluid_seg_z<T, LAST, P64, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
+                                              32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
+    return;
+  }
   constexpr int K = SegK<T>::K, SEG = 32 * K - 6;
   const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
   fluid_seg_z<T, LAST, P64, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
@@ -125,6 +132,13 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
     const size_t sm = march_smem<T>(15);
     if (axis == 0) ct_march_xy<T, 0, S, NT><<<grid, NT, sm, s>>>(g, in, out, h, ds);
     else ct_march_xy<T, 1, S, NT><<<grid, NT, sm, s>>>(g, in, out, h, ds);
+    return cudaGetLastError();
+  }
+  if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
+    constexpr int K = 2, SEG = 32 * K - 8;
+    const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
+    ct_seg_z<T, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps), 32 * kSegWarps, 0,
+                                s>>>(g, in, out, h, ds);
     return cudaGetLastError();
   }
   {

@@ -12,6 +12,20 @@
 
 namespace mhd {
 
+// Cells per lane of the FP32 z segments, chosen per grid: a window of 32K cells updates
+// 32K - 6 (fluid) or 32K - 8 (CT) of them, so short pencils waste part of a K = 3 window.
+// Work per pencil ~ windows x 32K x (cost per window cell), with the measured relative
+// costs 1.0 (K = 3) and 1.12 (K = 2); the cheaper choice is taken (the CT uses the fluid's
+// choice).  FP64 keeps K = 2.
+#ifndef MHD_SEG_K_AUTO
+#define MHD_SEG_K_AUTO 1
+#endif
+__host__ __device__ inline int seg_k_for(int nz) {
+  if (!MHD_SEG_K_AUTO) return 3;
+  const long long w3 = (nz + 89) / 90, w2 = (nz + 57) / 58;
+  return w2 * 64 * 112 < w3 * 96 * 100 ? 2 : 3;
+}
+
 // global loads: the read-only path in standalone kernels (NC), plain coherent loads where
 // the same launch writes the data earlier (the persistent batched kernel)
 template <bool NC, typename T>
