@@ -45,7 +45,7 @@ STEP_ALG_BYTES = 384
 # DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
 # a step) from ncu captures on a 256^3 grid (profiles/sweep_kernels_blast256_fp32.md), keyed
 # by the hash of the kernel sources they were taken on; another hash reports null.
-NCU_TRAFFIC_PER_CELL = {"f335f3b02e808c45": 50.61}
+NCU_TRAFFIC_PER_CELL = {"390e61aadcf2a474": 50.61}
 
 
 KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.cuh",
