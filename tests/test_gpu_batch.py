@@ -18,17 +18,20 @@ def mhd():
 
 
 def _problems():
-    # small uneven instances of the batched workload, one with mixed boundaries, one 2D
+    # small uneven instances of the batched workload, one with mixed boundaries, one 2D,
+    # and two whose x/y march blocks span several z rows or start inside a periodic z row
     probs = [I.batched_instance(i, lo=12, hi=40) for i in range(5)]
     probs.append(I.random_smooth((21, 9, 30), seed=21, bc=(1, 0, 1)))
     probs.append(I.orszag_tang(40, ny=28))
+    probs.append(I.random_smooth((20, 18, 36), seed=22, bc=(0, 1, 0)))
+    probs.append(I.random_smooth((6, 5, 132), seed=23))
     return probs
 
 
 @pytest.mark.parametrize("nsteps", [3, 4])
 def test_batch_matches_alone_bitwise(mhd, nsteps):
     probs = _problems()
-    pre = [0, 1, 2, 0, 1, 2, 1]          # instances start at different axis-order phases
+    pre = [0, 1, 2, 0, 1, 2, 1, 2, 0]    # instances start at different axis-order phases
     alone = []
     for p, k in zip(probs, pre):
         with mhd.Solver.from_problem(p, prec=mhd.FP32) as s:

@@ -68,6 +68,11 @@ OP_CASES = [
     ("zvec_outflow", lambda: I.random_smooth((13, 11, 72), seed=6, bc=(0, 1, 1))),
     ("zvec2_long", lambda: I.random_smooth((131, 6, 10), seed=15, bc=(1, 0, 0))),
     ("long_y", lambda: I.random_smooth((5, 150, 8), seed=16, bc=(0, 1, 1))),
+    # x/y march blocks of 128 pencils spanning several z rows (nz = 36), and blocks that
+    # start inside a periodic z row and end on its last pencil (nz = 132), with outflow
+    # across the other transverse axis
+    ("rows_per_block", lambda: I.random_smooth((9, 37, 36), seed=18)),
+    ("block_wraps_z", lambda: I.random_smooth((6, 5, 132), seed=19, bc=(1, 1, 0))),
 ]
 
 
