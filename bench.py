@@ -216,6 +216,20 @@ def oracle_sample(n: int, edge: int, steps: int) -> dict:
                       f"blast workload, FP64 oracle, OpenMP over pencils"}
 
 
+def oracle_single_core(n: int, edge: int) -> dict:
+    """The same oracle sample on one host core: a child process with OMP_NUM_THREADS=1
+    (the OpenMP runtime of this process has already fixed its thread count)."""
+    code = ("import json, bench; r = bench.oracle_sample(%d, %d, 1); "
+            "print(json.dumps({'value': r['value'], 'sample': r['sample']}))" % (n, edge))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": out["value"], "unit": UNIT, "cores": 1, "sample": out["sample"]}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -343,6 +357,7 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(n, args.cpu_edge, 1)
         cpu.pop("seconds", None)
+        cpu["single_core"] = oracle_single_core(n, min(64, args.cpu_edge))
 
     if rank == 0:
         step_ms = max_ms / args.steps
