@@ -46,6 +46,13 @@ STEP_ALG_BYTES = 384
 # a step) from ncu captures on a 256^3 grid (profiles/sweep_kernels_blast256_fp32.md), keyed
 # by the hash of the kernel sources they were taken on; another hash reports null.
 NCU_TRAFFIC_PER_CELL = {"390e61aadcf2a474": 50.61}
+# thread instructions per cell of one launch of each sweep kernel (ncu
+# smsp__thread_inst_executed.sum / cells, 256^3, the variants that do not reduce c_max),
+# keyed like the traffic: the sweeps are bound by instruction issue, and this gives the
+# issue rate they reach beside the HBM roofline
+NCU_INSTR_PER_CELL = {"390e61aadcf2a474": {"fluid_x": 348.7, "fluid_y": 349.8,
+                                           "fluid_z": 413.2, "ct_x": 222.2, "ct_y": 222.2,
+                                           "ct_z": 291.0}}
 
 
 KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.cuh",
@@ -359,6 +366,23 @@ def run_ours(args, world, rank, local):
         cpu.pop("seconds", None)
         cpu["single_core"] = oracle_single_core(n, min(64, args.cpu_edge))
 
+    issue = None
+    ipc = NCU_INSTR_PER_CELL.get(src_hash)
+    if ipc is not None:
+        ks = [k for k in ipc if k.startswith(dom + "_") and prof.get(k, (0, 0))[1]]
+        ins = sum(ipc[k] * N * prof[k][1] for k in ks)
+        tms = sum(prof[k][0] for k in ks)
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_i = sms * 4 * 32 * mhz * 1e6 / 1e12       # 4 schedulers x 32 lanes per SM
+        issue = {"kernel": f"{dom} sweep (all axes)", "unit": "T thread-instructions/s",
+                 "achieved": ins / (tms / 1e3) / 1e12, "peak": peak_i,
+                 "frac": ins / (tms / 1e3) / 1e12 / peak_i,
+                 "instr_per_cell": {k: ipc[k] for k in ks},
+                 "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz (median "
+                              f"SM clock of the timed region); instruction counts from ncu "
+                              f"on the same kernel sources"}
+
     if rank == 0:
         step_ms = max_ms / args.steps
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -373,6 +397,7 @@ def run_ours(args, world, rank, local):
                 "step_roofline": {"alg_bytes_per_cell": STEP_ALG_BYTES,
                                   "achieved": STEP_ALG_BYTES * N / (step_ms / 1e3) / 1e9,
                                   "frac": STEP_ALG_BYTES * N / (step_ms / 1e3) / 1e9 / peak},
+                "issue": issue,
                 "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
                 "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -35,6 +35,10 @@ def test_default_line_keys_small_grid():
     assert rl["bound"] == "hbm" and rl["unit"] == "GB/s"
     assert abs(rl["frac"] - rl["achieved"] / rl["peak"]) < 1e-9
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["single_core"]["cores"] == 1
+    iss = d["issue"]
+    if iss is not None:      # null when the kernel sources differ from the ncu capture's
+        assert 0 < iss["frac"] < 1.2 and abs(iss["frac"] - iss["achieved"] / iss["peak"]) < 1e-9
     e = d["e2e"]
     assert e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
