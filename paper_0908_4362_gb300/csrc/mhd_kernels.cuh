@@ -320,6 +320,21 @@ __global__ void dt_kernel(DevScalars* ds, double cfl_h) {
   dt_update<T>(ds, cfl_h);
 }
 
+// Exact float -> double by re-biasing the bits of normal numbers (and zeros) with integer
+// operations: GB300 executes the FP64 conversion at its low FP64 rate, which doubled the
+// cost of the sums.  Subnormals, infinities and NaN take the ordinary conversion.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  const bool zero = (b << 1) == 0u;
+  if ((e == 0u && !zero) || e == 0xffu) return (double)f;
+  const unsigned hi = zero ? (b & 0x80000000u)
+                           : (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  const unsigned lo = zero ? 0u : b << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // FP64 conservation sums: per-block partial sums (deterministic two-pass reduction)
 template <typename T>
 __global__ void sums_partial_kernel(long long N, FieldSet<T> in, double* partial) {
@@ -328,7 +343,7 @@ __global__ void sums_partial_kernel(long long N, FieldSet<T> in, double* partial
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] += (double)in.f[k][i];
+    for (int k = 0; k < 8; ++k) acc[k] += widen(in.f[k][i]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll

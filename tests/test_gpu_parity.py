@@ -276,6 +276,34 @@ def test_fp64_pressure_flag(mhd):
     assert np.all(errs[1] <= FP32_TOL)
 
 
+def test_fp32_sums_exact_widening(mhd):
+    """The FP64 sums of an FP32 state widen every value exactly (zeros of both signs,
+    subnormals, magnitudes over many decades): within FP64 accumulation error of the exact
+    sum of the stored values."""
+    import math
+    n = (16, 12, 20)
+    N = n[0] * n[1] * n[2]
+    rng = np.random.default_rng(31)
+    f = np.zeros((8, N), dtype=np.float32)
+    f[0] = 10.0 ** rng.uniform(-3, 3, N)
+    special = np.array([0.0, -0.0, 1e-40, -3e-42, 1e-20, -7.5, 2.0 ** -126], dtype=np.float32)
+    for k in (1, 2, 3, 5, 6, 7):
+        v = (rng.standard_normal(N) * 10.0 ** rng.uniform(-8, 1, N)).astype(np.float32)
+        pick = rng.random(N) < 0.3
+        v[pick] = special[rng.integers(0, len(special), pick.sum())]
+        f[k] = v
+    m2 = (f[1:4].astype(np.float64) ** 2).sum(0)
+    b2 = (f[5:8].astype(np.float64) ** 2).sum(0)
+    f[4] = (0.5 * m2 / f[0] + 0.5 * b2 + 10.0 ** rng.uniform(-2, 2, N)).astype(np.float32)
+    with mhd.Solver(n, (0, 0, 0), 1.0 / 20, 5.0 / 3.0, 0.7, prec=mhd.FP32) as s:
+        s.upload([f[k] for k in range(8)])
+        got = s.sums()
+    for k in range(8):
+        vals = f[k].astype(np.float64)
+        exact = math.fsum(vals.tolist())
+        assert abs(got[k] - exact) <= 1e-12 * np.abs(vals).sum() + 1e-300, (k, got[k], exact)
+
+
 def test_unphysical_state_reported(mhd):
     prob = I.random_smooth((8, 8, 8), seed=14)
     f = prob.fields.copy()
