@@ -12,7 +12,8 @@
 //
 // The operation order of each expression matches the oracle (phi(a/2, b/2) is evaluated
 // as phi(a, b)/2, which is the same rounded value), so the FP64 build without FMA
-// contraction reproduces it bit for bit.
+// contraction reproduces it bit for bit.  In FP32 every flux in the window is doubled
+// (cell_flux, FluxScale) and dth, hd come halved.
 #pragma once
 
 #include "mhd_kernels.cuh"
@@ -174,7 +175,7 @@ __device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const Fie
   const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
   const bool active = o_ < g.n[O];
-  const T dth = (T)(ds->dt / h);
+  const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
   const T hd = T(0.5) * dth;
   const int zc = min(z, g.n[2] - 1), oc = min(o, g.n[O] - 1);
   const long long base = (long long)zc + (long long)oc * g.s[O];

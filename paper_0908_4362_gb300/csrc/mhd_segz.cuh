@@ -133,7 +133,7 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
   const bool warp_active = pencil < npen;
   const long long pc = warp_active ? pencil : npen - 1;
   const int x = (int)(pc / g.n[1]), y = (int)(pc % g.n[1]);
-  const T dth = (T)(ds->dt / h);
+  const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
   const T hd = T(0.5) * dth;
   const long long row = (long long)x * g.s[0] + (long long)y * g.s[1];
   const long long r1 = row + (long long)(wrap_index(x + 1, g.n[0], g.bc[0]) - x) * g.s[0];
