@@ -356,7 +356,13 @@ __device__ __forceinline__ float2 half_vanleer2(float2 a, float2 b) {
   return make_float2(ab.x > 0.f ? q.x : 0.f, ab.y > 0.f ? q.y : 0.f);
 }
 
-// Two EmfPipe<float> in one: lane x and lane y are independent pipelines (same steps).
+// Two EmfPipe<float> in one: lane x and lane y are independent pipelines (same steps), with
+// the smoothed velocity kept as 4 vs (the (1,2,1) sum without its 1/4), so that g and every
+// EMF come out 4x EmfPipe's; ndth and nhd come divided by kEmf2Scale, and the edge velocity's
+// sign is that of vs(j) + vs(j+1).  The scales are powers of two, so they change the
+// rounding of none of the packed operations (the scalar constraint on B_A may be contracted
+// differently by the compiler: ulp-level differences, measured 2e-13 at 512^3).
+constexpr float kEmf2Scale = 4.f, kEmf2Inv = 0.25f;
 struct EmfPipe2 {
   float2 vf1, vf2, vs1, vs2, vs3, b1, b2, b3, b4, e1p, g3, g4, dp, pp, e2p;
 
@@ -365,17 +371,17 @@ struct EmfPipe2 {
         make_float2(0.f, 0.f);
   }
 
-  // ndth = -dt/h, nhd = -dt/(2h) in both lanes
+  // ndth = -dt/(4h), nhd = -dt/(8h) in both lanes (dt/h and dt/(2h) over kEmf2Scale)
   __device__ __forceinline__ float2 push(float2 vf0, float2 b0, float2 ndth, float2 nhd,
                                          float2* e2_prev) {
-    const float2 vs0 = mul2(splat2(0.25f), add2(fma2(splat2(2.f), vf1, vf0), vf2));
-    const float2 ve1 = mul2(splat2(0.5f), add2(vs1, vs0));
+    const float2 vs0 = add2(fma2(splat2(2.f), vf1, vf0), vf2);   // 4 vs(j-1)
+    const float2 ve1 = add2(vs1, vs0);                            // 8 x edge velocity
     const float2 e1 = sel_pos2(ve1, mul2(vs1, b2), mul2(vs0, b1));
     const float2 bh = fma2(nhd, sub2(e1, e1p), b2);
     const float2 g2 = mul2(vs1, bh);
     const float2 dn = sub2(g2, g3);
     const float2 pn = half_vanleer2(dp, dn);
-    const float2 ve4 = mul2(splat2(0.5f), add2(vs3, vs2));
+    const float2 ve4 = add2(vs3, vs2);
     const float2 e2 = sel_pos2(ve4, add2(g4, pp), sub2(g3, pn));
     const float2 bt = fma2(ndth, sub2(e2, e2p), b4);
     *e2_prev = e2p;
@@ -435,7 +441,7 @@ struct CtColumn {
     const T vn2 = hx2 ? Num<T>::div(m[4] + m[3], r[4] + r[3]) : Num<T>::div(m[4] + m[0], r[4] + r[0]);
     T eo1, en1, eo2, en2;
     if constexpr (PACK) {
-      const float2 ndth = splat2(-(float)dth), nhd = splat2(-(float)hd);
+      const float2 ndth = splat2(-(float)dth * kEmf2Inv), nhd = splat2(-(float)hd * kEmf2Inv);
       float2 eo, en;
       const float2 bt = ownp.push(make_float2((float)vo1, (float)vo2),
                                   make_float2((float)b1o, (float)b2o), ndth, nhd, &eo);
@@ -449,8 +455,9 @@ struct CtColumn {
       *bt2 = own2.push(vo2, b2o, dth, hd, &eo2);
       nb2.push(vn2, b2h, dth, hd, &en2);
     }
-    T b = ba4 + dth * (en1 - eo1);           // constraint from t1, then t2
-    b = b + dth * (en2 - eo2);
+    const T dc = PACK ? dth * T(kEmf2Inv) : dth;   // the packed EMFs are kEmf2Scale x
+    T b = ba4 + dc * (en1 - eo1);            // constraint from t1, then t2
+    b = b + dc * (en2 - eo2);
     *bA = b;
     ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = ba;
   }
@@ -611,7 +618,8 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
   p1.init();
   p2.init();
   pp2.init();
-  const float2 ndth2 = splat2(-(float)dth), nhd2 = splat2(-(float)hd);
+  const float2 ndth2 = splat2(-(float)dth * kEmf2Inv), nhd2 = splat2(-(float)hd * kEmf2Inv);
+  const T dc = PACK ? dth * T(kEmf2Inv) : dth;   // constraint factor for the EMFs' scale
   T ba1 = T(0), ba2 = T(0), ba3 = T(0), ba4 = T(0);
   const int js = a0 - 4;
   const int kend = min(S, nA - a0) + 8;
@@ -673,8 +681,8 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
     const T eo_up = xb[halo_row ? threadIdx.x : threadIdx.x + 32];
     const T ez_up = __shfl_down_sync(0xffffffffu, Z1 ? e1 : e2, 1);
     const T en1 = Z1 ? ez_up : eo_up, en2 = Z1 ? eo_up : ez_up;
-    T b = ba4 + dth * (en1 - e1);            // constraint from t1, then t2
-    b = b + dth * (en2 - e2);
+    T b = ba4 + dc * (en1 - e1);             // constraint from t1, then t2
+    b = b + dc * (en2 - e2);
     ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = slot[8 * NT];
     if (k >= 8 && out_ok) {
       const long long co = base + (long long)(j - 4) * sA;

@@ -287,7 +287,8 @@ __device__ __forceinline__ void emf_seg(const T (&vf)[K], T (&bt)[K], T dth, T h
 }
 
 // emf_seg<float> of two pipelines at once (lane x and lane y of each float2), f32x2
-// arithmetic
+// arithmetic, with the scales of EmfPipe2: vs kept as 4 vs, EMFs kEmf2Scale x emf_seg's,
+// ndth and nhd divided by kEmf2Scale (powers of two: no packed operation rounds differently)
 template <int K>
 __device__ __forceinline__ void emf_seg2(const float2 (&vf)[K], float2 (&bt)[K], float2 ndth,
                                          float2 nhd, float2 (&e2m)[K]) {
@@ -296,15 +297,14 @@ __device__ __forceinline__ void emf_seg2(const float2 (&vf)[K], float2 (&bt)[K],
   next_cell2<K>(vf, vn);
   prev_cell2<K>(vf, vp);
 #pragma unroll
-  for (int i = 0; i < K; ++i)
-    vs[i] = mul2(splat2(0.25f), add2(fma2(splat2(2.f), vf[i], vn[i]), vp[i]));
+  for (int i = 0; i < K; ++i) vs[i] = add2(fma2(splat2(2.f), vf[i], vn[i]), vp[i]);   // 4 vs
   next_cell2<K>(vs, vsn);
 #pragma unroll
   for (int i = 0; i < K; ++i) f[i] = mul2(vs[i], bt[i]);
   next_cell2<K>(f, fn);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    ve[i] = mul2(splat2(0.5f), add2(vs[i], vsn[i]));            // edge velocity at +1/2
+    ve[i] = add2(vs[i], vsn[i]);                                 // 8 x edge velocity
     e1[i] = sel_pos2(ve[i], f[i], fn[i]);                        // first-order EMF
   }
   prev_cell2<K>(e1, e1p);
@@ -373,7 +373,9 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
                              : Num<T>::div(m[4] + m[0], r[4] + r[0]);
   }
   T eo1[K], en1[K], eo2[K], en2[K];
-  if constexpr (sizeof(T) == 4 && MHD_CT_PACK) {
+  constexpr bool PACK = sizeof(T) == 4 && MHD_CT_PACK;
+  const T dc = PACK ? dth * T(kEmf2Inv) : dth;   // constraint factor for the EMFs' scale
+  if constexpr (PACK) {
     // the own-row pipelines of t1 and t2 as one packed pair, the upper-row ones as another
     float2 vo[K], vn[K], bo[K], bh[K], eo[K], en[K];
 #pragma unroll
@@ -383,7 +385,8 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
       bo[i] = make_float2(b1o[i], b2o[i]);
       bh[i] = make_float2(b1h[i], b2h[i]);
     }
-    const float2 ndth2 = splat2(-(float)dth), nhd2 = splat2(-(float)hd);
+    const float2 ndth2 = splat2(-(float)dth * kEmf2Inv);
+    const float2 nhd2 = splat2(-(float)hd * kEmf2Inv);
     emf_seg2<K>(vo, bo, ndth2, nhd2, eo);
     emf_seg2<K>(vn, bh, ndth2, nhd2, en);
 #pragma unroll
@@ -402,8 +405,8 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const int w = lane * K + i, z = z0 + i;
-    T bA = ba[i] + dth * (en1[i] - eo1[i]);      // constraint from t1 = x, then t2 = y
-    bA = bA + dth * (en2[i] - eo2[i]);
+    T bA = ba[i] + dc * (en1[i] - eo1[i]);       // constraint from t1 = x, then t2 = y
+    bA = bA + dc * (en2[i] - eo2[i]);
     if (warp_active && w >= H && w < H + SEG && z < nz) {
       const long long co = row + z;
       out.f[5][co] = b1o[i];
