@@ -26,6 +26,27 @@ __host__ __device__ inline int seg_k_for(int nz) {
   return w2 * 64 * 112 < w3 * 96 * 100 ? 2 : 3;
 }
 
+// Which window a warp takes: segment s of pencil (x, y), the segments of a pencil on
+// consecutive warps (ordering consecutive warps along y at a fixed segment, so that a
+// block's warps share their y-neighbour rows in L1, measured 2.6% slower for the fluid).
+// Warps past the end are inactive and take the last window for their arithmetic.
+struct SegPlace {
+  int s0, x, y;
+  bool active;
+};
+__device__ __forceinline__ SegPlace seg_place(const GridDesc& g, int nz, int seg, long long wid) {
+  const int nseg = (nz + seg - 1) / seg;
+  const long long total = (long long)g.n[0] * g.n[1] * nseg;
+  SegPlace p;
+  p.active = wid < total;
+  const long long w = p.active ? wid : total - 1;
+  const long long pencil = w / nseg;
+  p.s0 = (int)(w % nseg) * seg;
+  p.x = (int)(pencil / g.n[1]);
+  p.y = (int)(pencil % g.n[1]);
+  return p;
+}
+
 // global loads: the read-only path in standalone kernels (NC), plain coherent loads where
 // the same launch writes the data earlier (the persistent batched kernel)
 template <bool NC, typename T>
@@ -118,7 +139,7 @@ __device__ __forceinline__ void seg_stage2(const V (&fr2)[K], const V (&fl2)[K],
   for (int i = 0; i < K; ++i) un[i] = Vec<V>::fnma(dth, Vec<V>::sub(g2[i], g2p[i]), u[i]);
 }
 
-// one warp: segment `wid` (pencil wid / nseg, segment wid % nseg); all 32 lanes call it
+// one warp: window `wid` (seg_place); all 32 lanes call it
 template <typename T, bool LAST, bool P64, int K, bool NC>
 __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                                  const FieldSet<T>& out, T gamma, double h,
@@ -126,13 +147,9 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
   constexpr int H = 3, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
-  const int nseg = (nz + SEG - 1) / SEG;
-  const long long pencil = wid / nseg;
-  const int s0 = (int)(wid % nseg) * SEG;
-  const long long npen = (long long)g.n[0] * g.n[1];
-  const bool warp_active = pencil < npen;
-  const long long pc = warp_active ? pencil : npen - 1;
-  const int x = (int)(pc / g.n[1]), y = (int)(pc % g.n[1]);
+  const SegPlace sp = seg_place(g, nz, SEG, wid);
+  const int s0 = sp.s0, x = sp.x, y = sp.y;
+  const bool warp_active = sp.active;
   const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
   const T hd = T(0.5) * dth;
   const long long row = (long long)x * g.s[0] + (long long)y * g.s[1];
@@ -333,13 +350,9 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
   constexpr int H = 4, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
-  const int nseg = (nz + SEG - 1) / SEG;
-  const long long pencil = wid / nseg;
-  const int s0 = (int)(wid % nseg) * SEG;
-  const long long npen = (long long)g.n[0] * g.n[1];
-  const bool warp_active = pencil < npen;
-  const long long pc = warp_active ? pencil : npen - 1;
-  const int x = (int)(pc / g.n[1]), y = (int)(pc % g.n[1]);
+  const SegPlace sp = seg_place(g, nz, SEG, wid);
+  const int s0 = sp.s0, x = sp.x, y = sp.y;
+  const bool warp_active = sp.active;
   const T dth = (T)(ds->dt / h);
   const T hd = T(0.5) * dth;
   const long long row = (long long)x * g.s[0] + (long long)y * g.s[1];
