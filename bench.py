@@ -64,6 +64,8 @@ def kernel_source_hash() -> str:
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_0908_4362_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_0908_4362_gb300", "build.py"), "rb") as fh:
+        h.update(fh.read())          # the compiler flags are part of the kernels
     return h.hexdigest()[:16]
 
 

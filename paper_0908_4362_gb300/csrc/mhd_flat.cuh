@@ -52,8 +52,8 @@ __device__ __forceinline__ T ct_flat_cell(const GridDesc& g, const FieldSet<T>& 
     e[q][0] = Num<T>::mul_rn(vo, pb[i]);
     e[q][1] = Num<T>::mul_rn(vn, pb[ihi]);
   }
-  T b = in.f[5 + A][i] + dth * (e[0][1] - e[0][0]);   // constraint from t1, then t2
-  b = b + dth * (e[1][1] - e[1][0]);
+  T b = ffma(dth, e[0][1] - e[0][0], in.f[5 + A][i]);   // constraint from t1, then t2
+  b = ffma(dth, e[1][1] - e[1][0], b);
   return b;
 }
 

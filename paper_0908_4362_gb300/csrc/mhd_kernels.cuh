@@ -94,6 +94,21 @@ template <> struct Num<double> {
   }
 };
 
+// a b + c and b - s a: one fused, singly rounded operation in FP32, two in FP64.  The FP32
+// kernels are built without automatic contraction, so every fusion is written here and
+// rounds the same in every kernel that inlines the expression (a grid's result does not
+// depend on which kernel advanced it); FP64 keeps the oracle's separately rounded steps.
+template <typename T>
+__device__ __forceinline__ T ffma(T a, T b, T c) {
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c);
+  else return a * b + c;
+}
+template <typename T>
+__device__ __forceinline__ T ffms(T s, T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fmaf_rn(-s, a, b);
+  else return b - s * a;
+}
+
 __device__ __forceinline__ int wrap_index(int i, int n, int bc) {
   if (i >= 0 && i < n) return i;
   if (bc == 0) {
@@ -130,32 +145,33 @@ __device__ __forceinline__ int cell_flux(const T u[5], const T b[3], T gamma, T 
     // relaxed fluxes c u +- F (the same quantities, fewer instructions)
     const T ir = T(1) / rho;
     const T vn = u[1] * ir, vt1 = u[2] * ir, vt2 = u[3] * ir;
-    const T b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const T b2 = __fmaf_rn(b[2], b[2], __fmaf_rn(b[1], b[1], b[0] * b[0]));
     T p;
     if (P64) {
       const double m1 = u[1], m2 = u[2], m3 = u[3];
       const double bb0 = b[0], bb1 = b[1], bb2 = b[2];
-      const double ke = 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / (double)rho;
-      p = (T)(((double)gamma - 1.0) * ((double)u[4] - ke - 0.5 * (bb0 * bb0 + bb1 * bb1 + bb2 * bb2)));
+      const double ke = 0.5 * __fma_rn(m3, m3, __fma_rn(m2, m2, m1 * m1)) / (double)rho;
+      const double bb = __fma_rn(bb2, bb2, __fma_rn(bb1, bb1, bb0 * bb0));
+      p = (T)(((double)gamma - 1.0) * __fma_rn(-0.5, bb, (double)u[4] - ke));
     } else {
-      const T mv = u[1] * vn + u[2] * vt1 + u[3] * vt2;
-      p = (gamma - T(1)) * (u[4] - T(0.5) * mv - T(0.5) * b2);
+      const T mv = __fmaf_rn(u[3], vt2, __fmaf_rn(u[2], vt1, u[1] * vn));
+      p = (gamma - T(1)) * __fmaf_rn(T(-0.5), b2, __fmaf_rn(T(-0.5), mv, u[4]));
     }
-    const T ps = p + T(0.5) * b2;
-    const T bv = b[0] * vn + b[1] * vt1 + b[2] * vt2;
+    const T ps = __fmaf_rn(T(0.5), b2, p);
+    const T bv = __fmaf_rn(b[2], vt2, __fmaf_rn(b[1], vt1, b[0] * vn));
     T F[5];
     F[0] = u[1];
-    F[1] = u[1] * vn + ps - b[0] * b[0];
-    F[2] = u[2] * vn - b[0] * b[1];
-    F[3] = u[3] * vn - b[0] * b[2];
-    F[4] = (u[4] + ps) * vn - b[0] * bv;
-    const T rad = (gamma * p + b2) * ir;
+    F[1] = __fmaf_rn(-b[0], b[0], __fmaf_rn(u[1], vn, ps));
+    F[2] = __fmaf_rn(-b[0], b[1], u[2] * vn);
+    F[3] = __fmaf_rn(-b[0], b[2], u[3] * vn);
+    F[4] = __fmaf_rn(-b[0], bv, (u[4] + ps) * vn);
+    const T rad = __fmaf_rn(gamma, p, b2) * ir;
     const int st = (!(rho > T(0)) || rad < T(0)) ? ST_UNPHYSICAL : 0;
     const T c = fabs(vn) + sqrtf(rad);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      fr[k] = c * u[k] + F[k];
-      fl[k] = c * u[k] - F[k];
+      fr[k] = __fmaf_rn(c, u[k], F[k]);
+      fl[k] = __fmaf_rn(c, u[k], -F[k]);
     }
     return st;
   } else {
@@ -196,6 +212,29 @@ __device__ __forceinline__ T half_vanleer(T a, T b) {
   }
 }
 
+// base + phi(a, b)/2 and base - phi(a, b)/2 (the limited corrections of Eq. "eq:F_n"): in
+// FP32 the quotient ab/(a+b) is ab times an approximate reciprocal, fused into the sum
+template <typename T>
+__device__ __forceinline__ T plus_half_vanleer(T base, T a, T b) {
+  if constexpr (sizeof(T) == 4) {
+    const T ab = a * b;
+    const T r = __fdividef(T(1), a + b);
+    return ab > T(0) ? __fmaf_rn(ab, r, base) : base;
+  } else {
+    return base + half_vanleer(a, b);
+  }
+}
+template <typename T>
+__device__ __forceinline__ T minus_half_vanleer(T base, T a, T b) {
+  if constexpr (sizeof(T) == 4) {
+    const T ab = a * b;
+    const T r = __fdividef(T(1), a + b);
+    return ab > T(0) ? __fmaf_rn(-ab, r, base) : base;
+  } else {
+    return base - half_vanleer(a, b);
+  }
+}
+
 // |v|^2 and |B|^2 summed smallest first, so that c_max does not depend on axis order.
 template <typename T>
 __device__ __forceinline__ T sum3_sorted(T a, T b, T c) {
@@ -218,7 +257,7 @@ __device__ __forceinline__ T cell_cmax(T rho, T m0, T m1, T m2, T E, T b0, T b1,
     const double ke = 0.5 * (mm0 * mm0 + mm1 * mm1 + mm2 * mm2) / rd;
     p = (T)(((double)gamma - 1.0) * ((double)E - ke - 0.5 * (c0 * c0 + c1 * c1 + c2 * c2)));
   } else {
-    p = (gamma - T(1)) * (E - T(0.5) * rho * vv - T(0.5) * bb);
+    p = (gamma - T(1)) * ffms(T(0.5), bb, ffms(T(0.5) * rho, vv, E));
   }
   const T rad = Num<T>::div(gamma * p, rho) + Num<T>::div(bb, rho);
   if (!(rho > T(0)) || rad < T(0)) *st |= ST_UNPHYSICAL;

@@ -53,7 +53,7 @@ struct FluidPencil {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const T g1c = fr1[c] - fl0[c];                 // first-order flux at (j-1)+1/2
-      uh[c] = u1[c] - hd * (g1c - g1[c]);            // u^{t+dt/2}(j-1)
+      uh[c] = ffms(hd, g1c - g1[c], u1[c]);          // u^{t+dt/2}(j-1)
       g1[c] = g1c;
       fr1[c] = fr0[c];
     }
@@ -64,9 +64,9 @@ struct FluidPencil {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const T dRc = frB[c] - frA[c];                 // FR2(j-2) - FR2(j-3)
-      const T right = frA[c] + half_vanleer(dRp[c], dRc);
+      const T right = plus_half_vanleer(frA[c], dRp[c], dRc);
       const T dLc = fl2[c] - flL[c];                 // FL2(j-1) - FL2(j-2)
-      const T left = flL[c] - half_vanleer(dLp[c], dLc);
+      const T left = minus_half_vanleer(flL[c], dLp[c], dLc);
       g2c[c] = right - left;                         // limited flux at (j-3)+1/2
       dRp[c] = dRc;
       frA[c] = frB[c];
@@ -77,7 +77,7 @@ struct FluidPencil {
     const bool valid = k >= 6;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      out[c] = u3[c] - dth * (g2c[c] - g2[c]);
+      out[c] = ffms(dth, g2c[c] - g2[c], u3[c]);
       g2[c] = g2c[c];
       u3[c] = u2[c];
       u2[c] = u1[c];
@@ -124,12 +124,10 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // prefetch depth (iterations ahead) and ring length of the marching kernels
-// (at 512^3, 3 iterations ahead ran 1.7% faster for the fluid and 1.1% for the CT than 4,
-// but the compiler then contracted the FP32 arithmetic of the tile differently inside the
-// persistent batched kernel than in the single-grid kernel, so a grid's result would depend
-// on the path that advanced it; 5 was no better, 6 slower)
+// (at 512^3, 3 iterations ahead run 1.2% faster for the fluid and 1.1% for the CT than 4;
+// 5 was no better, 6 slower)
 #ifndef MHD_MARCH_DEPTH
-#define MHD_MARCH_DEPTH 4
+#define MHD_MARCH_DEPTH 3
 #endif
 constexpr int kMarchDepth = MHD_MARCH_DEPTH;
 constexpr int kMarchRing = kMarchDepth + 1;
@@ -465,8 +463,8 @@ struct CtColumn {
       nb2.push(vn2, b2h, dth, hd, &en2);
     }
     const T dc = PACK ? dth * T(kEmf2Inv) : dth;   // the packed EMFs are kEmf2Scale x
-    T b = ba4 + dc * (en1 - eo1);            // constraint from t1, then t2
-    b = b + dc * (en2 - eo2);
+    T b = ffma(dc, en1 - eo1, ba4);          // constraint from t1, then t2
+    b = ffma(dc, en2 - eo2, b);
     *bA = b;
     ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = ba;
   }
@@ -690,8 +688,8 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
     const T eo_up = xb[halo_row ? threadIdx.x : threadIdx.x + 32];
     const T ez_up = __shfl_down_sync(0xffffffffu, Z1 ? e1 : e2, 1);
     const T en1 = Z1 ? ez_up : eo_up, en2 = Z1 ? eo_up : ez_up;
-    T b = ba4 + dc * (en1 - e1);             // constraint from t1, then t2
-    b = b + dc * (en2 - e2);
+    T b = ffma(dc, en1 - e1, ba4);           // constraint from t1, then t2
+    b = ffma(dc, en2 - e2, b);
     ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = slot[8 * NT];
     if (k >= 8 && out_ok) {
       const long long co = base + (long long)(j - 4) * sA;

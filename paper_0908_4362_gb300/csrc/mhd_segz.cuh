@@ -94,8 +94,9 @@ __device__ __forceinline__ void prev_cell2(const float2 (&x)[K], float2 (&xp)[K]
 template <typename T> struct Vec {
   static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
   static __device__ __forceinline__ T add(T a, T b) { return a + b; }
-  static __device__ __forceinline__ T fnma(T s, T a, T b) { return b - s * a; }   // b - s a
-  static __device__ __forceinline__ T hv(T a, T b) { return half_vanleer(a, b); }
+  static __device__ __forceinline__ T fnma(T s, T a, T b) { return ffms(s, a, b); }   // b - s a
+  static __device__ __forceinline__ T add_hv(T base, T a, T b) { return plus_half_vanleer(base, a, b); }
+  static __device__ __forceinline__ T sub_hv(T base, T a, T b) { return minus_half_vanleer(base, a, b); }
   static __device__ __forceinline__ T splat(T v) { return v; }
   template <int K>
   static __device__ __forceinline__ void next(const T (&x)[K], T (&xn)[K]) { next_cell<T, K>(x, xn); }
@@ -130,8 +131,8 @@ __device__ __forceinline__ void seg_stage2(const V (&fr2)[K], const V (&fl2)[K],
   Vec<V>::template next<K>(dL, dLn);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    const V right = Vec<V>::add(fr2[i], Vec<V>::hv(dRp[i], dR[i]));
-    const V left = Vec<V>::sub(fln[i], Vec<V>::hv(dL[i], dLn[i]));
+    const V right = Vec<V>::add_hv(fr2[i], dRp[i], dR[i]);
+    const V left = Vec<V>::sub_hv(fln[i], dL[i], dLn[i]);
     g2[i] = Vec<V>::sub(right, left);                                // limited flux at +1/2
   }
   Vec<V>::template prev<K>(g2, g2p);
@@ -418,8 +419,8 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const int w = lane * K + i, z = z0 + i;
-    T bA = ba[i] + dc * (en1[i] - eo1[i]);       // constraint from t1 = x, then t2 = y
-    bA = bA + dc * (en2[i] - eo2[i]);
+    T bA = ffma(dc, en1[i] - eo1[i], ba[i]);     // constraint from t1 = x, then t2 = y
+    bA = ffma(dc, en2[i] - eo2[i], bA);
     if (warp_active && w >= H && w < H + SEG && z < nz) {
       const long long co = row + z;
       out.f[5][co] = b1o[i];

@@ -202,7 +202,7 @@ def blast2d(n: int = 512, cfl: float = 0.7, t_end: float = 0.2) -> Problem:
     return Problem(f"blast2d_{n}", shape, (PERIODIC,) * 3, h, gamma, cfl, f, t_end)
 
 
-def rotor(n: int = 512, variant: int = 1, cfl: float = 0.7) -> Problem:
+def rotor(n: int = 512, variant: int = 1, cfl: float = 0.7, offset=(0.0, 0.0)) -> Problem:
     """MHD rotor of Sect. 5.2.3 on the unit square, nz = 1, outflow in x and y.
 
     A dense disk (rho = 10, r < r0 = 0.1 about (0.5, 0.5)) rotates rigidly at angular
@@ -212,7 +212,8 @@ def rotor(n: int = 512, variant: int = 1, cfl: float = 0.7) -> Problem:
     variant 2: v0 = 1, p = 0.5, gamma = 5/3, B0 = 2.5/sqrt(4 pi), t_max = 0.295.
     Readings: the taper's v_y is printed as -f v0 (x - 0.5)/r, whose sign would reverse the
     rotation across r0 (the disk's v_y is +v0 (x - 0.5)/r0); it is read as +f v0 (x-0.5)/r.
-    The boundary type is not stated; outflow (zero gradient) is used."""
+    The boundary type is not stated; outflow (zero gradient) is used.  `offset` moves the
+    disk's centre (box units; the paper's is 0, 0)."""
     if variant == 1:
         v0, p0, gamma, b0, t_end = 2.0, 1.0, 1.4, 5.0 / math.sqrt(4 * math.pi), 0.15
     elif variant == 2:
@@ -222,8 +223,8 @@ def rotor(n: int = 512, variant: int = 1, cfl: float = 0.7) -> Problem:
     r0, r1 = 0.1, 0.115
     h = 1.0 / n
     xc = _centres(n, h)
-    X = (xc - 0.5)[:, None, None] * np.ones((1, n, 1))
-    Y = (xc - 0.5)[None, :, None] * np.ones((n, 1, 1))
+    X = (xc - 0.5 - offset[0])[:, None, None] * np.ones((1, n, 1))
+    Y = (xc - 0.5 - offset[1])[None, :, None] * np.ones((n, 1, 1))
     r = np.sqrt(X * X + Y * Y)
     f = (r1 - r) / (r1 - r0)
     inner, taper = r < r0, (r >= r0) & (r < r1)
