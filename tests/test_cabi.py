@@ -42,3 +42,15 @@ def test_missing_library_fails_loudly(tmp_path):
     import pytest
     with pytest.raises(ImportError):
         mhd.load_library(str(tmp_path / "nope.so"))
+
+
+def test_fp32_units_build_without_automatic_contraction():
+    """The FP32 sweep bodies are inlined into the single-grid kernels and into the persistent
+    batched kernel; both units must be built without automatic FMA contraction (the fusions
+    are written out), or the two paths could round differently."""
+    from paper_0908_4362_gb300 import build
+    flags = dict(build.UNITS)
+    for unit in ("kernels_f32.cu", "mhd_batch.cu"):
+        assert "--fmad=false" in flags[unit] and "--use_fast_math" not in flags[unit], unit
+    assert flags["kernels_f32.cu"] == flags["mhd_batch.cu"]
+    assert "--fmad=false" in flags["kernels_f64.cu"]
