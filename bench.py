@@ -45,12 +45,12 @@ STEP_ALG_BYTES = 384
 # DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
 # a step) from ncu captures on a 256^3 grid (profiles/sweep_kernels_blast256_fp32.md), keyed
 # by the hash of the kernel sources they were taken on; another hash reports null.
-NCU_TRAFFIC_PER_CELL = {"c7a9c2bb06f80b93": 50.78}
+NCU_TRAFFIC_PER_CELL = {"5fc818fba809cbc8": 50.66}
 # thread instructions per cell of one launch of each sweep kernel (ncu
 # smsp__thread_inst_executed.sum / cells, 256^3, the variants that do not reduce c_max),
 # keyed like the traffic: the sweeps are bound by instruction issue, and this gives the
 # issue rate they reach beside the HBM roofline
-NCU_INSTR_PER_CELL = {"c7a9c2bb06f80b93": {"fluid_x": 319.2, "fluid_y": 319.2,
+NCU_INSTR_PER_CELL = {"5fc818fba809cbc8": {"fluid_x": 319.2, "fluid_y": 319.2,
                                            "fluid_z": 381.5, "ct_x": 199.5, "ct_y": 199.5,
                                            "ct_z": 286.7}}
 

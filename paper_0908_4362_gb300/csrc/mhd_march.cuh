@@ -367,8 +367,7 @@ __device__ __forceinline__ float2 half_vanleer2(float2 a, float2 b) {
 // the smoothed velocity kept as 4 vs (the (1,2,1) sum without its 1/4), so that g and every
 // EMF come out 4x EmfPipe's; ndth and nhd come divided by kEmf2Scale, and the edge velocity's
 // sign is that of vs(j) + vs(j+1).  The scales are powers of two, so they change the
-// rounding of none of the packed operations (the scalar constraint on B_A may be contracted
-// differently by the compiler: ulp-level differences, measured 2e-13 at 512^3).
+// rounding of none of the packed operations.
 constexpr float kEmf2Scale = 4.f, kEmf2Inv = 0.25f;
 struct EmfPipe2 {
   float2 vf1, vf2, vs1, vs2, vs3, b1, b2, b3, b4, e1p, g3, g4, dp, pp, e2p;
