@@ -59,6 +59,29 @@ KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.
                   "mhd_launch_impl.cuh")
 
 
+def issue_object(dom: str, prof: dict, ipc: dict | None, cells: int, sms: int,
+                 mhz: float) -> dict | None:
+    """Instruction-issue rate of the `dom` sweeps: ncu thread instructions per cell of each
+    kernel kind (`ipc`, None when the counts are not of these kernel sources) x cells x
+    launches, over their total live time (`prof`: kind -> (ms, launches)), against the SMs'
+    issue peak (4 schedulers x 32 lanes per SM per clock)."""
+    if ipc is None:
+        return None
+    ks = [k for k in ipc if k.startswith(dom + "_") and prof.get(k, (0, 0))[1]]
+    tms = sum(prof[k][0] for k in ks)
+    if not ks or tms <= 0:
+        return None
+    ins = sum(ipc[k] * cells * prof[k][1] for k in ks)
+    peak = sms * 4 * 32 * mhz * 1e6 / 1e12
+    achieved = ins / (tms / 1e3) / 1e12
+    return {"kernel": f"{dom} sweep (all axes)", "unit": "T thread-instructions/s",
+            "achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "instr_per_cell": {k: ipc[k] for k in ks},
+            "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz (median SM "
+                         f"clock of the timed region); instruction counts from ncu on the "
+                         f"same kernel sources"}
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -368,22 +391,9 @@ def run_ours(args, world, rank, local):
         cpu.pop("seconds", None)
         cpu["single_core"] = oracle_single_core(n, min(64, args.cpu_edge))
 
-    issue = None
-    ipc = NCU_INSTR_PER_CELL.get(src_hash)
-    if ipc is not None:
-        ks = [k for k in ipc if k.startswith(dom + "_") and prof.get(k, (0, 0))[1]]
-        ins = sum(ipc[k] * N * prof[k][1] for k in ks)
-        tms = sum(prof[k][0] for k in ks)
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = (clk or {}).get("sm_mhz") or 2070.0
-        peak_i = sms * 4 * 32 * mhz * 1e6 / 1e12       # 4 schedulers x 32 lanes per SM
-        issue = {"kernel": f"{dom} sweep (all axes)", "unit": "T thread-instructions/s",
-                 "achieved": ins / (tms / 1e3) / 1e12, "peak": peak_i,
-                 "frac": ins / (tms / 1e3) / 1e12 / peak_i,
-                 "instr_per_cell": {k: ipc[k] for k in ks},
-                 "peak_note": f"{sms} SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz (median "
-                              f"SM clock of the timed region); instruction counts from ncu "
-                              f"on the same kernel sources"}
+    issue = issue_object(dom, prof, NCU_INSTR_PER_CELL.get(src_hash), N,
+                         torch.cuda.get_device_properties(local).multi_processor_count,
+                         (clk or {}).get("sm_mhz") or 2070.0)
 
     if rank == 0:
         step_ms = max_ms / args.steps
