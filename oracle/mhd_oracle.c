@@ -7,7 +7,7 @@
  * that the CUDA path is compared against.  Only the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark may load it.  It shares no code with the CUDA path.
  *
- * Conventions (all readings listed in the design doc):
+ * Conventions (where the paper is silent, the reading taken is stated beside the code):
  *   - 8 fields per cell, f[0..7] = (rho, rho vx, rho vy, rho vz, E, Bx, By, Bz), Sect. 4.1.
  *   - Flat index (x*ny + y)*nz + z, z contiguous (Sect. 4.1, index equations).
  *   - B is face-centred (Eq. "equat_b"): Bx[i] lives on the x-face i-1/2, By[j] on y-face
@@ -270,7 +270,14 @@ static void emf_pencil(const orc_grid* g, double* const f[8], int a, int tsel, i
 #endif
         bt[e] = f[5 + t][c0];
     }
-    for (int e = 1; e + 1 < L; ++e) vs[e] = 0.25 * (vf[e + 1] + 2.0 * vf[e] + vf[e - 1]);
+    /* (1,2,1)/4 with the two outer neighbours added first: the sum is then exactly odd
+     * under a reflection of the a-axis (v_a -> -v_a, neighbours swapped), so the edge
+     * velocity at a mirror face is exactly 0 and Eq. "eq:first_flux"'s rule decides it */
+#if ORC_MUTANT == 14
+    for (int e = 1; e + 1 < L; ++e) vs[e] = 0.25 * (vf[e + 1] + 2.0 * vf[e] + vf[e - 1]);  /* mistake: one-sided order */
+#else
+    for (int e = 1; e + 1 < L; ++e) vs[e] = 0.25 * ((vf[e + 1] + vf[e - 1]) + 2.0 * vf[e]);
+#endif
     /* first-order upwind EMF by the sign of the edge velocity, Eq. "eq:first_flux" */
     for (int e = 1; e + 2 < L; ++e) {
         double ve = 0.5 * (vs[e] + vs[e + 1]);

@@ -286,6 +286,10 @@ namespace mhd {
 // ------------------------------------------------------------------------------------
 // Marching constrained transport (Algorithm 2; Eqs. "eq:averaging_x", "eq:first_flux").
 // One EMF pipeline follows one pencil of a transverse face component B_t along the sweep.
+// The (1,2,1) smoothing adds the two outer face velocities first: the smoothed velocity is
+// then exactly odd under a reflection of the sweep axis, so the edge velocity on a mirror
+// face is exactly 0 in every precision and the upwind rule of Eq. "eq:first_flux" (0 takes
+// the right cell) decides it the same way in FP32 as in FP64.
 // Pushing cell j (face velocity vf(j) across the t-face and B_t(j)) yields, 4 cells
 // behind, the advected B_t(j-4) and the limited EMF at the A-face (j-4)+1/2; the EMF at
 // (j-5)+1/2 (the previous one) is what the constraint on B_A(j-4) uses.
@@ -308,7 +312,7 @@ struct EmfPipe {
 
   // returns the advected B_t(j-4); e2_prev receives the EMF at (j-5)+1/2
   __device__ __forceinline__ T push(T vf0, T b0, T dth, T hd, T* e2_prev) {
-    const T vs0 = T(0.25) * (vf0 + T(2) * vf1 + vf2);           // vs(j-1)
+    const T vs0 = T(0.25) * ((vf0 + vf2) + T(2) * vf1);         // vs(j-1)
     const T ve1 = T(0.5) * (vs1 + vs0);                           // edge velocity (j-2)+1/2
     const T e1 = ve1 > T(0) ? vs1 * b2 : vs0 * b1;               // first-order EMF (j-2)+1/2
     const T bh = b2 - hd * (e1 - e1p);                            // B_t(j-2) at t + dt/2
@@ -380,7 +384,7 @@ struct EmfPipe2 {
   // ndth = -dt/(4h), nhd = -dt/(8h) in both lanes (dt/h and dt/(2h) over kEmf2Scale)
   __device__ __forceinline__ float2 push(float2 vf0, float2 b0, float2 ndth, float2 nhd,
                                          float2* e2_prev) {
-    const float2 vs0 = add2(fma2(splat2(2.f), vf1, vf0), vf2);   // 4 vs(j-1)
+    const float2 vs0 = fma2(splat2(2.f), vf1, add2(vf0, vf2));   // 4 vs(j-1)
     const float2 ve1 = add2(vs1, vs0);                            // 8 x edge velocity
     const float2 e1 = sel_pos2(ve1, mul2(vs1, b2), mul2(vs0, b1));
     const float2 bh = fma2(nhd, sub2(e1, e1p), b2);

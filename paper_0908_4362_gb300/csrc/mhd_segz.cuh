@@ -273,7 +273,7 @@ __device__ __forceinline__ void emf_seg(const T (&vf)[K], T (&bt)[K], T dth, T h
   next_cell<T, K>(vf, vn);
   prev_cell<T, K>(vf, vp);
 #pragma unroll
-  for (int i = 0; i < K; ++i) vs[i] = T(0.25) * (vn[i] + T(2) * vf[i] + vp[i]);
+  for (int i = 0; i < K; ++i) vs[i] = T(0.25) * ((vn[i] + vp[i]) + T(2) * vf[i]);
   next_cell<T, K>(vs, vsn);
 #pragma unroll
   for (int i = 0; i < K; ++i) f[i] = vs[i] * bt[i];
@@ -315,7 +315,7 @@ __device__ __forceinline__ void emf_seg2(const float2 (&vf)[K], float2 (&bt)[K],
   next_cell2<K>(vf, vn);
   prev_cell2<K>(vf, vp);
 #pragma unroll
-  for (int i = 0; i < K; ++i) vs[i] = add2(fma2(splat2(2.f), vf[i], vn[i]), vp[i]);   // 4 vs
+  for (int i = 0; i < K; ++i) vs[i] = fma2(splat2(2.f), vf[i], add2(vn[i], vp[i]));   // 4 vs
   next_cell2<K>(vs, vsn);
 #pragma unroll
   for (int i = 0; i < K; ++i) f[i] = mul2(vs[i], bt[i]);

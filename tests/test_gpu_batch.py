@@ -4,7 +4,9 @@ bounded device wait of the persistent kernel gives up with MHD_ERR_TIMEOUT."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_0908_4362_gb300 import inputs as I
+from parity import FP32_TOL, rel_l1
 
 pytestmark = pytest.mark.gpu
 
@@ -47,12 +49,38 @@ def test_batch_matches_alone_bitwise(mhd, nsteps):
         assert b.sync() == mhd.MHD_OK
         ctas, items = b.info()
         assert ctas > 0 and items > 0
-    for s, ref, k in zip(solvers, alone, pre):
+    for s, ref, k, p in zip(solvers, alone, pre, probs):
         got = s.read()
         t, _, stp, ph = s.state()
         assert stp == k + 2 * nsteps and ph == (k + 2 * nsteps) % 3
         assert np.array_equal(got, ref)
         s.close()
+        # and the batched result against the FP64 oracle run from the same input (the
+        # initial state rounded to FP32, as the FP32 context holds it), at the FP32
+        # tolerance
+        f32 = p.fields.astype(np.float32).astype(np.float64)
+        o = oracle.Oracle(p.n, p.bc, p.h, p.gamma, p.cfl, f32)
+        o.step(k + 2 * nsteps)
+        assert abs(t - o.t) <= FP32_TOL * o.t
+        err = rel_l1(got, o.f)
+        assert np.all(err <= FP32_TOL), (p.name, err)
+
+
+def test_batch_full_size_instances_vs_oracle(mhd):
+    """Four instances of the batched workload at their own sizes (edges 48..192), 10 steps in
+    one persistent launch, against the FP64 oracle at the FP32 tolerance."""
+    probs = [I.batched_instance(i) for i in range(4)]
+    solvers = [mhd.Solver.from_problem(p, prec=mhd.FP32) for p in probs]
+    with mhd.Batch(solvers) as b:
+        b.step(10)
+        assert b.sync() == mhd.MHD_OK
+    for s, p in zip(solvers, probs):
+        got = s.read()
+        s.close()
+        o = oracle.Oracle.from_problem(p)
+        o.step(10)
+        err = rel_l1(got, o.f)
+        assert np.all(err <= FP32_TOL), (p.name, err)
 
 
 def test_batch_rejects_fp64_context(mhd):

@@ -23,6 +23,7 @@ MUTANTS = {
     11: ("time step not scaled by the cell width", ["entropy_wave", "sod"]),
     12: ("a step advances dt instead of 2 dt", ["entropy_wave", "sod"]),
     13: ("predictor over a full dt", ["entropy_wave", "sod"]),
+    14: ("(1,2,1) smoothing summed from one side", ["mirror"]),
 }
 
 
