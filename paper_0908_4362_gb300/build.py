@@ -42,10 +42,15 @@ def _sources_mtime() -> float:
     return max(os.path.getmtime(f) for f in files if os.path.isfile(f))
 
 
+# extra preprocessor definitions for every unit (tuning knobs of the kernels, e.g.
+# "-DMHD_CT_CHUNK=4"); empty by default
+DEFS = os.environ.get("MHD_NVCC_DEFS", "").split()
+
+
 def _compile(src: str, extra: list, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [NVCC, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), *extra, os.path.join(CSRC, src), "-o", obj]
+           "-I", os.path.join(ROOT, "include"), *DEFS, *extra, os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -395,8 +395,10 @@ mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int c
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_inst, inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_abort, 0, sizeof(int) * 2);
-  // shared memory: the larger march prefetch ring (CT, 15 values per iteration)
-  b->smem = sizeof(float) * (size_t)mhd::kMarchRing * 15 * mhd::kBatchNT;
+  // shared memory: the largest tile body (the per-element CT march's prefetch ring, 15 values
+  // per iteration, or the 16-byte fluid staging)
+  b->smem = std::max({sizeof(float) * (size_t)mhd::kMarchRing * 15 * mhd::kBatchNT,
+                      mhd::march_tile_smem<float>(), mhd::ct_rows_smem<float>(mhd::kBatchRowsR)});
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mhd::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)b->smem);

@@ -23,8 +23,16 @@ template <typename T> struct SegK { static constexpr int K = sizeof(T) == 4 ? MH
 
 template <typename T, int A, bool LAST, bool P64>
 static cudaError_t set_march_attr() {
-  return cudaFuncSetAttribute(fluid_march_xy<T, A, LAST, P64, MarchCfg<T>::S, MarchCfg<T>::NT>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem<T>(10));
+  cudaError_t e = cudaFuncSetAttribute(
+      fluid_march_xy<T, A, LAST, P64, MarchCfg<T>::S, MarchCfg<T>::NT>,
+      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
+  if constexpr (sizeof(T) == 4) {
+    const cudaError_t e2 = cudaFuncSetAttribute(
+        fluid_march_xy_vec<A, LAST, P64, MarchCfg<T>::S, MarchCfg<T>::NT>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
+    if (e2 != cudaSuccess) e = e2;
+  }
+  return e;
 }
 template <typename T, int A>
 static cudaError_t set_ct_march_attr() {
@@ -63,7 +71,14 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
     const int o = axis == 0 ? 1 : 0;
     const long long np = (long long)g.n[2] * g.n[o];
     const dim3 grid((unsigned)((np + NT - 1) / NT), (unsigned)((g.n[axis] + S - 1) / S));
-    const size_t sm = march_smem<T>(10);
+    const size_t sm = march_tile_smem<T>();
+    if constexpr (sizeof(T) == 4) {
+      if (march_vec<T>(g)) {
+        if (axis == 0) fluid_march_xy_vec<0, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        else fluid_march_xy_vec<1, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        return;
+      }
+    }
     if (axis == 0) fluid_march_xy<T, 0, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
     else fluid_march_xy<T, 1, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
     return;

@@ -168,10 +168,10 @@ constexpr int kCtUnroll = MHD_CT_UNROLL;
 // one tile: pencils bx*NT .. bx*NT+NT-1 of the transverse plane, cells by*S .. by*S+S-1
 // along the sweep; smem_raw holds the prefetch ring (march_ring_bytes)
 template <typename T, int A, bool LAST, bool P64, int S, int NT>
-__device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const FieldSet<T>& in,
-                                                    const FieldSet<T>& out, T gamma, double h,
-                                                    DevScalars* ds, unsigned bx, unsigned by,
-                                                    unsigned char* smem_raw) {
+__device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, const FieldSet<T>& in,
+                                                         const FieldSet<T>& out, T gamma, double h,
+                                                         DevScalars* ds, unsigned bx, unsigned by,
+                                                         unsigned char* smem_raw) {
   static_assert(A == 0 || A == 1, "x or y sweep");
   constexpr int O = (A == 0) ? 1 : 0;       // the transverse axis that is not z
   constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
@@ -271,12 +271,176 @@ __device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const Fie
   if (active && P.st) atomicOr(&ds->status, P.st);
 }
 
+// 16-byte staging (FP32, nz a multiple of 4).  Each warp stages its own 32 pencils: 8 groups
+// of 4 consecutive z positions, which never straddle a z row and start on a 16-byte
+// boundary.  Per cell along the sweep the warp needs 9 rows of 32 values (u, B_n one cell
+// ahead, B_t1, B_t2, and the B across the other transverse axis O one row up); lane l copies
+// group l % 8 of rows l / 8 and 4 + l / 8 (lanes 0-7 also row 8) with one 16-byte cp.async
+// each: about 2.3 copies and addresses per thread and cell instead of 10.  The z + 1
+// neighbour of B_z is the next lane's B_z, except for lane 31 and at the end of a z row
+// (wrapped or clamped), where the thread copies it itself into row 9.  Lanes read each
+// other's copies after their own cp.async wait and a warp barrier; no block barrier, so
+// warps march independently as in the per-element staging.
+constexpr int kVecRows = 10;
+
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <int A, bool LAST, bool P64, int S, int NT>
+__device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const FieldSet<float>& in,
+                                                        const FieldSet<float>& out, float gamma,
+                                                        double h, DevScalars* ds, unsigned bx,
+                                                        unsigned by, unsigned char* smem_raw) {
+  static_assert(A == 0 || A == 1, "x or y sweep");
+  static_assert(NT % 32 == 0, "whole warps");
+  using T = float;
+  constexpr int O = (A == 0) ? 1 : 0;       // the transverse axis that is not z
+  constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int nz = g.n[2], nO = g.n[O];
+  const long long ntr = (long long)nz * nO;  // pencils of the transverse plane
+  const long long p = (long long)bx * NT + tid;
+  const bool active = p < ntr;
+  const int z = (int)(p % nz);
+  const int o = active ? (int)(p / nz) : nO - 1;
+  const int a0 = by * S;
+  const int nA = g.n[A], bcA = g.bc[A];
+  const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);
+  const T hd = T(0.5) * dth;
+  const long long sA = g.s[A], sO = g.s[O];
+  // this lane's copies: group q of rows r and r + 4 (and of row 8 for lanes 0-7)
+  const int q = lane & 7, r = lane >> 3;
+  const long long pq = (long long)bx * NT + 32 * w + 4 * q;
+  const bool gq = pq < ntr;
+  const int zq = (int)(pq % nz), oq = gq ? (int)(pq / nz) : 0;
+  const long long tq = (long long)zq + (long long)oq * sO;
+  const long long tq8 = (long long)zq + (long long)wrap_index(oq + 1, nO, g.bc[O]) * sO;
+  // rows 0-3: rho, m_A, m_T1, m_T2; rows 4-7: E, B_A (one cell ahead), B_T1, B_T2; row 8:
+  // the B across O, one O row up
+  const float* src0 = (r == 0 ? in.f[0] : r == 1 ? in.f[1 + A] : r == 2 ? in.f[1 + T1]
+                                                                         : in.f[1 + T2]) + tq;
+  const float* src1 = (r == 0 ? in.f[4] : r == 1 ? in.f[5 + A] : r == 2 ? in.f[5 + T1]
+                                                                         : in.f[5 + T2]) + tq;
+  const float* src2 = in.f[5 + (A == 0 ? T1 : T2)] + tq8;
+  // the z + 1 neighbour of B_z that the next lane does not hold
+  const bool special = active && (lane == 31 || z == nz - 1);
+  const float* srcs = in.f[7] + (long long)wrap_index(z + 1, nz, g.bc[2]) + (long long)o * sO;
+  constexpr int RS = kVecRows * 32;          // floats per ring slot of a warp
+  float* ring = reinterpret_cast<float*>(smem_raw) + (size_t)w * kMarchRing * RS;
+  const int js = a0 - 3;
+  const int kend = min(S, nA - a0) + 6;
+  auto issue = [&](int kk) {
+    if (kk < kend) {
+      const long long off = (long long)wrap_index(js + kk, nA, bcA) * sA;
+      float* slot = ring + (size_t)(kk % kMarchRing) * RS + 4 * q;
+      if (gq) {
+        const long long off1 = r == 1 ? (long long)wrap_index(js + kk + 1, nA, bcA) * sA : off;
+        cp_async_16(slot + r * 32, src0 + off);
+        cp_async_16(slot + (4 + r) * 32, src1 + off1);
+        if (lane < 8) cp_async_16(slot + 8 * 32, src2 + off);
+      }
+      if (special) cp_async_elem(ring + (size_t)(kk % kMarchRing) * RS + 9 * 32 + lane, srcs + off);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < kMarchDepth; ++d) issue(d);
+  FluidPencil<T, P64, LAST> P;
+  P.init();
+  const long long base = (long long)z + (long long)o * sO;
+  T bn_cur = in.f[5 + A][base + wrap_off<T>(js, nA, bcA, sA)];
+  T cm = T(0);
+  bool nan_seen = false;
+  constexpr int ZROW = (A == 0) ? 7 : 6;     // the row holding B_z (B_t2 for x, B_t1 for y)
+  const int nb_idx = special ? 9 * 32 + lane : ZROW * 32 + lane + 1;
+#pragma unroll kFluidUnroll
+  for (int k = 0; k < kend; ++k) {
+    cp_async_wait<kMarchDepth - 1>();
+    __syncwarp();
+    issue(k + kMarchDepth);
+    const float* slot = ring + (size_t)(k % kMarchRing) * RS;
+    const int j = js + k;
+    T u0[5], b0[3];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) u0[c] = slot[c * 32 + lane];
+    const T bn_next = slot[5 * 32 + lane];
+    const T zb_nb = slot[nb_idx];
+    const T ob_nb = slot[8 * 32 + lane];
+    b0[0] = T(0.5) * (bn_cur + bn_next);
+    b0[1] = T(0.5) * (slot[6 * 32 + lane] + (A == 0 ? ob_nb : zb_nb));
+    b0[2] = T(0.5) * (slot[7 * 32 + lane] + (A == 0 ? zb_nb : ob_nb));
+    bn_cur = bn_next;
+    T un[5], bo[3];
+    if (P.push(k, u0, b0, gamma, dth, hd, un, bo)) {
+      const int ia = j - 3;
+      if (active) {
+        const long long co = base + (long long)ia * sA;
+        out.f[0][co] = un[0];
+        out.f[1 + A][co] = un[1];
+        out.f[1 + T1][co] = un[2];
+        out.f[1 + T2][co] = un[3];
+        out.f[4][co] = un[4];
+        if (!(un[0] > T(0))) P.st |= ST_UNPHYSICAL;
+        if (LAST) {
+          const T v = cell_cmax<T, P64>(un[0], un[1], un[2], un[3], un[4], bo[0], bo[1], bo[2],
+                                        gamma, &P.st);
+          if (v != v) nan_seen = true; else cm = fmax(cm, v);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (LAST) block_max_to_global(cm, nan_seen, ds);
+  if (active && P.st) atomicOr(&ds->status, P.st);
+}
+
+// FP32 grids whose z extent is a multiple of 4 take the 16-byte staging, others the
+// per-element one; both feed the same arithmetic in the same order (identical results)
+template <typename T>
+__host__ __device__ inline bool march_vec(const GridDesc& g) {
+  return sizeof(T) == 4 && g.n[2] % 4 == 0;
+}
+template <typename T>
+static size_t march_tile_smem() {
+  return sizeof(T) * (size_t)kMarchRing * kVecRows * 128;   // both stagings: 10 values per cell
+}
+
+template <typename T, int A, bool LAST, bool P64, int S, int NT>
+__device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const FieldSet<T>& in,
+                                                    const FieldSet<T>& out, T gamma, double h,
+                                                    DevScalars* ds, unsigned bx, unsigned by,
+                                                    unsigned char* smem_raw) {
+  if constexpr (sizeof(T) == 4 && NT == 128) {
+    if (march_vec<T>(g)) {
+      fluid_march_xy_tile_vec<A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, bx, by, smem_raw);
+      return;
+    }
+  }
+  fluid_march_xy_tile_elem<T, A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, bx, by, smem_raw);
+}
+
 template <typename T, int A, bool LAST, bool P64, int S, int NT>
 __global__ void __launch_bounds__(NT, MHD_MARCH_MINB)
 fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fluid_march_xy_tile<T, A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, blockIdx.x, blockIdx.y,
-                                              smem_raw);
+  fluid_march_xy_tile_elem<T, A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, blockIdx.x,
+                                                   blockIdx.y, smem_raw);
+}
+
+// the 16-byte staging as a kernel of its own (its register allocation does not carry the
+// per-element path's); MHD_VEC_MINB resident blocks per SM asked of the compiler
+#ifndef MHD_VEC_MINB
+#define MHD_VEC_MINB 4
+#endif
+template <int A, bool LAST, bool P64, int S, int NT>
+__global__ void __launch_bounds__(NT, MHD_VEC_MINB)
+fluid_march_xy_vec(GridDesc g, FieldSet<float> in, FieldSet<float> out, float gamma, double h,
+                   DevScalars* ds) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fluid_march_xy_tile_vec<A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, blockIdx.x, blockIdx.y,
+                                               smem_raw);
 }
 
 }  // namespace mhd
