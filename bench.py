@@ -172,6 +172,20 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def start_clocks(local: int) -> "ClockSampler":
+    """A running nvidia-smi sampler of the rank's GPU (stop() returns the clock record)."""
+    import torch
+    dev_uuid = None
+    try:
+        dev_uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    c = ClockSampler(dev_uuid)
+    c.start()
+    time.sleep(0.3)
+    return c
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -452,6 +466,7 @@ def run_batched(args, world, rank, local):
     for _ in range(max(1, args.warmup // per_call)):
         batch.step(per_call)
     assert batch.sync() == mhd.MHD_OK
+    clocks = start_clocks(local)
     ms_b = timed(batch.stream_handle(), lambda: [batch.step(per_call) for _ in range(k // per_call)])
     assert batch.sync() == mhd.MHD_OK
     ctas, items = batch.info()
@@ -465,6 +480,7 @@ def run_batched(args, world, rank, local):
         s_.step(max(1, args.warmup // per_call) * per_call)
     torch.cuda.synchronize()
     ms_p = timed(shared.cuda_stream, lambda: [s_.step(k) for s_ in sp])
+    clk = clocks.stop()
     identical = all(np.array_equal(a.read(), b.read()) for a, b in zip(sb[:8], sp[:8]))
     batch.close()
     for s_ in sb + sp:
@@ -481,7 +497,8 @@ def run_batched(args, world, rank, local):
                 "plain": {"value": cells * k / (ms_p / 1e3), "ms_per_step": ms_p / k,
                           "how": "mhd_step per instance, one after another on one stream"},
                 "speedup_vs_plain": ms_p / ms_b, "results_identical": identical,
-                "autotune": tune, "resident_ctas": ctas, "items_per_launch": items}
+                "autotune": tune, "resident_ctas": ctas, "items_per_launch": items,
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -521,6 +538,7 @@ def run_serving(args, world, rank, local):
     warm = [dataclasses.replace(r, steps=6) for r in base[:8]]
     serve.Server(be, budget, ics=ics).run(warm)
     serve.serve_sequential(be, warm[:2], ics=ics)
+    clocks = start_clocks(local)
     # saturation: capacity of each form on the same requests
     calib = [dataclasses.replace(r, arrival=0.0) for r in base[:args.calib]]
     sat_srv = serve.Server(be, budget, ics=ics)
@@ -532,6 +550,7 @@ def run_serving(args, world, rank, local):
     srv = serve.Server(be, budget, ics=ics, keep_results=digest)
     jobs = srv.run(trace)
     seq = serve.serve_sequential(be, trace, ics=ics, keep_results=digest)
+    clk = clocks.stop()
     same = sum(a.result.result() == b.result.result()
                for a, b in zip(sorted(jobs, key=lambda j: j.req.rid),
                                sorted(seq, key=lambda j: j.req.rid)))
@@ -561,7 +580,7 @@ def run_serving(args, world, rank, local):
                 "iterations": srv.iterations, "batch_rebuilds": srv.batch_rebuilds,
                 "host_seconds": {k: round(v, 3) for k, v in srv.times.items()},
                 "results_identical_alone_vs_mix": f"{same}/{len(jobs)}",
-                "initial_states_s": t_ic}
+                "initial_states_s": t_ic, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -591,6 +610,7 @@ def run_vis(args, world, rank, local):
         return e0.elapsed_time(e1) / reps
 
     res = {}
+    clocks = start_clocks(local)
     with mhd.Solver.from_problem(I.orszag_tang(512), prec=mhd.FP32) as s:
         s.step(30, sync=True)
         lo, hi = s.vis_range("rho")
@@ -602,6 +622,7 @@ def run_vis(args, world, rank, local):
             for axis in (0, 2):
                 res[f"volume_blast{n}_axis{axis}_ms"] = frames(
                     s, lambda: s.vis_volume("p", axis, lo, hi, 0.02), reps=5)
+    clk = clocks.stop()
     if rank == 0:
         line = {"metric": "frames/s (headless visualization kernels)",
                 "value": 1e3 / res["slice_ot512_ms"], "unit": "frames/s", "n_gpus": world,
@@ -614,7 +635,8 @@ def run_vis(args, world, rank, local):
                                      "its stream synchronisation"},
                 "frame_ms": res,
                 "note": "the paper's OpenGL frame rates are unavailable on this box (no "
-                        "graphics stack); these are the CUDA kernels producing the same images"}
+                        "graphics stack); these are the CUDA kernels producing the same images",
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -630,10 +652,13 @@ def _rel_l1_fields(a, b):
 
 
 def run_precision(args, world, rank, local):
-    """The precision variants on a 256^3 blast: FP32 sweeps, FP32 with the FP64 pressure
-    recovery, and the FP64 parity path (built without FMA contraction; bit-identical to the
-    FP64 oracle in the parity tests).  Each FP32 variant's state after the same 13 steps is
-    compared with the FP64 path's (relative L1 per field)."""
+    """The precision variants on the 256^3 blast: FP32 sweeps with the pressure recovered in
+    plain FP32, in FP64, and in compensated FP32 (error-free sums and products), and the FP64
+    parity path (built without FMA contraction; bit-identical to the FP64 oracle in the
+    parity tests).  Each FP32 variant's state after the same 13 steps is compared with the
+    FP64 path's (relative L1 per field).  The pressure-recovery variants differ from plain
+    FP32 mainly where the thermal energy is a small part of E (low beta, high Mach number);
+    the parity tests check that case."""
     import numpy as np
     import torch
 
@@ -643,13 +668,16 @@ def run_precision(args, world, rank, local):
     build.build()
     torch.cuda.set_device(local)
     n = 256
-    prob = I.blast3d(n, offset=(0.37, -0.21, 0.13))
+    prob = I.blast3d(n)
     res = {}
     ref = None
-    for name, prec, p64 in (("fp64", mhd.FP64, False), ("fp32", mhd.FP32, False),
-                            ("fp32_fp64_pressure", mhd.FP32, True)):
+    clocks = start_clocks(local)
+    for name, prec, pm in (("fp64", mhd.FP64, mhd.PRESSURE_FP32),
+                           ("fp32", mhd.FP32, mhd.PRESSURE_FP32),
+                           ("fp32_fp64_pressure", mhd.FP32, mhd.PRESSURE_FP64),
+                           ("fp32_compensated_pressure", mhd.FP32, mhd.PRESSURE_COMPENSATED)):
         with mhd.Solver(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, prec=prec,
-                        fp64_pressure=p64) as s:
+                        pressure=pm) as s:
             s.init_fields(prob.fields)
             s.step(3, sync=True)
             st = torch.cuda.ExternalStream(s.stream_handle())
@@ -670,16 +698,17 @@ def run_precision(args, world, rank, local):
                 res[name]["rel_l1_vs_fp64_per_field"] = err
                 res[name]["max_rel_l1_vs_fp64"] = max(err)
             del state
+    clk = clocks.stop()
     if rank == 0:
         line = {"metric": "cell-updates/s by precision (256^3 blast)",
                 "value": res["fp64"]["cell_updates_per_s"], "unit": UNIT, "n_gpus": world,
                 "steps": 10, "warmup": 3, "ms_per_step": res["fp64"]["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "3D magnetised blast 256^3 (off-centre), periodic",
+                "config": {"workload": "3D magnetised blast 256^3, periodic",
                            "error": "state after 13 steps vs the FP64 path's (each variant "
                                     "takes its own dt from its own c_max)"},
-                "variants": res}
+                "variants": res, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 

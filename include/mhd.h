@@ -50,6 +50,13 @@ typedef enum {
 
 typedef enum { MHD_BC_PERIODIC = 0, MHD_BC_OUTFLOW = 1 } mhd_bc;
 typedef enum { MHD_FP32 = 0, MHD_FP64 = 1 } mhd_precision;
+/* How the FP32 sweeps recover the pressure p = (gamma-1)(E - |m|^2/(2 rho) - |B|^2/2) (the
+ * equation of state of Sect. 3), which cancels when the plasma beta is low: plain FP32, FP64
+ * arithmetic, or compensated FP32 (error-free sums and products carry the rounding errors
+ * of the two quadratic terms and of the subtractions: the exactly rounded p of the FP32
+ * inputs, as FP64 gives it, at FP32 speed).  Selected by mhd_config.fp64_pressure. */
+typedef enum { MHD_PRESSURE_FP32 = 0, MHD_PRESSURE_FP64 = 1, MHD_PRESSURE_COMPENSATED = 2 }
+    mhd_pressure_mode;
 
 typedef struct {
   int nx, ny, nz;        /* cells per axis, each >= 1 */
@@ -58,7 +65,7 @@ typedef struct {
   double cfl;            /* Courant number, 0 < cfl < 1 (paper: ~0.7) */
   int bc[3];             /* mhd_bc per axis */
   int prec;              /* mhd_precision of the device state and arithmetic */
-  int fp64_pressure;     /* FP32 only: recover p = (gamma-1)(E - rho v^2/2 - B^2/2) in FP64 */
+  int fp64_pressure;     /* mhd_pressure_mode of the pressure recovery; FP64 contexts: 0 */
   void* cuda_stream;     /* cudaStream_t to run on; NULL: the context creates its own */
 } mhd_config;
 

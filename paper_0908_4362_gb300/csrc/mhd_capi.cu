@@ -92,7 +92,7 @@ static cudaError_t enqueue_fluid(mhd_ctx* ctx, int axis, bool last) {
   ProfScope ps(ctx, axis);
   FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
   cudaError_t e = Launch<T>::fluid(ctx->g, in, out, ctx->cfg.gamma, ctx->cfg.h, ctx->ds, axis,
-                                   last, ctx->cfg.fp64_pressure != 0, ctx->stream);
+                                   last, ctx->cfg.fp64_pressure, ctx->stream);
   if (!mhd::axis_is_flat(ctx->g, axis))   // along a flat axis the sweep is the identity
     for (int k = 0; k < 5; ++k) ctx->cur[k] ^= 1;
   return e;
@@ -189,11 +189,11 @@ static mhd_status compute_cmax(mhd_ctx* ctx) {
   cudaError_t e;
   if (ctx->esz == 4) {
     f32 = fields_of<float>(ctx, false);
-    e = Launch<float>::cmax(ctx->g, f32, ctx->cfg.gamma, ctx->ds, ctx->cfg.fp64_pressure != 0,
+    e = Launch<float>::cmax(ctx->g, f32, ctx->cfg.gamma, ctx->ds, ctx->cfg.fp64_pressure,
                             ctx->stream);
   } else {
     f64 = fields_of<double>(ctx, false);
-    e = Launch<double>::cmax(ctx->g, f64, ctx->cfg.gamma, ctx->ds, false, ctx->stream);
+    e = Launch<double>::cmax(ctx->g, f64, ctx->cfg.gamma, ctx->ds, 0, ctx->stream);
   }
   CK(e, "cmax");
   return MHD_OK;
@@ -243,6 +243,8 @@ static mhd_status validate(const mhd_config* c) {
   for (int a = 0; a < 3; ++a)
     if (c->bc[a] != MHD_BC_PERIODIC && c->bc[a] != MHD_BC_OUTFLOW) return MHD_ERR_INVALID;
   if (c->prec != MHD_FP32 && c->prec != MHD_FP64) return MHD_ERR_INVALID;
+  if (c->fp64_pressure < MHD_PRESSURE_FP32 || c->fp64_pressure > MHD_PRESSURE_COMPENSATED)
+    return MHD_ERR_INVALID;
   if (c->prec == MHD_FP64 && c->fp64_pressure) return MHD_ERR_INVALID;
   return MHD_OK;
 }

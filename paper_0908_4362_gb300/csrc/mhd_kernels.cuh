@@ -126,18 +126,68 @@ __device__ __forceinline__ T vanleer(T a, T b) {
   return ab > T(0) ? Num<T>::div(T(2) * ab, a + b) : T(0);
 }
 
+// Pressure recovery modes of the FP32 sweeps (the context's pressure mode): 0 plain FP32,
+// 1 FP64 arithmetic, 2 compensated FP32.  p = (gamma-1)(E - m^2/(2 rho) - B^2/2) cancels at
+// low plasma beta, where E is dominated by B^2/2; plain FP32 loses log2(E/p) bits of p.
+enum : int { PM_FP32 = 0, PM_FP64 = 1, PM_COMP = 2 };
+
+// Error-free transformations in round-to-nearest FP32: a + b = s + e exactly (Knuth's
+// TwoSum, TAOCP vol. 2, Sect. 4.2.2) and a b = p + e exactly (Dekker's product, its error
+// term taken with one fused multiply-add).  Written with explicitly rounded operations so
+// that no compiler contraction changes them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+// x^2 + y^2 + z^2 as an unevaluated sum hi + lo (double-float), exact to ~2^-44 relative
+__device__ __forceinline__ void sumsq_df(float x, float y, float z, float& hi, float& lo) {
+  float p1, e1, p2, e2, p3, e3, s, t1, t2;
+  two_prod(x, x, p1, e1);
+  two_prod(y, y, p2, e2);
+  two_prod(z, z, p3, e3);
+  two_sum(p1, p2, s, t1);
+  two_sum(s, p3, hi, t2);
+  lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), e3), __fadd_rn(t1, t2));
+}
+// p = (gamma-1)(E - |m|^2/(2 rho) - |B|^2/2) in double-float FP32 arithmetic: the two
+// quadratic terms and the two cancelling subtractions keep their rounding errors, so p comes
+// out as the FP32 rounding of the exact value for the given FP32 inputs (as FP64 arithmetic
+// would give it), at a fraction of GB300's FP64 cost.  gm1 = gamma - 1, ir ~ 1/rho (an
+// approximate reciprocal is enough: the remainder below absorbs its error).
+__device__ __forceinline__ float pressure_comp(float rho, float ir, float m1, float m2, float m3,
+                                               float E, float b0, float b1, float b2, float gm1) {
+  float mh, ml, bh, bl;
+  sumsq_df(m1, m2, m3, mh, ml);
+  sumsq_df(b0, b1, b2, bh, bl);
+  // |m|^2 / rho = q + ql: q an approximate quotient, its remainder mh - q rho by one FMA
+  // (exact to ~2^-46 of mh for a quotient within a few ulps)
+  const float q = __fmul_rn(mh, ir);
+  const float r = __fmaf_rn(-q, rho, mh);
+  const float ql = __fmul_rn(__fadd_rn(r, ml), ir);
+  float x1, f1, x2, f2;
+  two_sum(E, -0.5f * q, x1, f1);
+  two_sum(x1, -0.5f * bh, x2, f2);
+  const float tail = __fadd_rn(__fadd_rn(f1, f2), -0.5f * __fadd_rn(ql, bl));
+  return __fmaf_rn(gm1, x2, __fmul_rn(gm1, tail));
+}
+
 // Cell flux in local coordinates, Eqs. "eq:flux" and "eq:lr": returns the fluxes of the
 // right- and left-moving variables, fr = (c u + F)/2 and fl = (c u - F)/2, with the
 // freezing speed c = |v_n| + sqrt(gamma p/rho + B^2/rho) -- scaled by FluxScale<T>::out:
 // FP32 returns c u + F and c u - F (twice the fluxes, six fewer multiplications per cell),
 // and its callers take half step factors; a power-of-two scale commutes with rounding.
-// P64: recover the pressure in double precision (low-beta cancellation in E - B^2/2).
+// PM: the pressure recovery mode (PM_FP32, PM_FP64, PM_COMP), FP32 only.
 template <typename T> struct FluxScale {
   static constexpr double out = sizeof(T) == 4 ? 2.0 : 1.0;   // cell_flux result / fluxes
   static constexpr double inv = 1.0 / out;                    // factor on dt/h, dt/(2h)
 };
 
-template <typename T, bool P64>
+template <typename T, int PM>
 __device__ __forceinline__ int cell_flux(const T u[5], const T b[3], T gamma, T fr[5], T fl[5]) {
   const T rho = u[0];
   if constexpr (sizeof(T) == 4) {
@@ -147,7 +197,9 @@ __device__ __forceinline__ int cell_flux(const T u[5], const T b[3], T gamma, T 
     const T vn = u[1] * ir, vt1 = u[2] * ir, vt2 = u[3] * ir;
     const T b2 = __fmaf_rn(b[2], b[2], __fmaf_rn(b[1], b[1], b[0] * b[0]));
     T p;
-    if (P64) {
+    if (PM == PM_COMP) {
+      p = pressure_comp(rho, ir, u[1], u[2], u[3], u[4], b[0], b[1], b[2], gamma - T(1));
+    } else if (PM == PM_FP64) {
       const double m1 = u[1], m2 = u[2], m3 = u[3];
       const double bb0 = b[0], bb1 = b[1], bb2 = b[2];
       const double ke = 0.5 * __fma_rn(m3, m3, __fma_rn(m2, m2, m1 * m1)) / (double)rho;
@@ -245,14 +297,24 @@ __device__ __forceinline__ T sum3_sorted(T a, T b, T c) {
 }
 
 // CFL speed of one cell, Eq. "equat_CFL": max(|vx|,|vy|,|vz|) + sqrt(gamma p/rho + B^2/rho).
-template <typename T, bool P64>
+template <typename T, int PM>
 __device__ __forceinline__ T cell_cmax(T rho, T m0, T m1, T m2, T E, T b0, T b1, T b2, T gamma,
                                        int* st) {
   const T v0 = Num<T>::div(m0, rho), v1 = Num<T>::div(m1, rho), v2 = Num<T>::div(m2, rho);
   const T vv = sum3_sorted(v0 * v0, v1 * v1, v2 * v2);
   const T bb = sum3_sorted(b0 * b0, b1 * b1, b2 * b2);
   T p;
-  if (P64) {
+  if constexpr (PM == PM_COMP && sizeof(T) == 4) {
+    // the three squares of each sum in a fixed order of magnitude, as sum3_sorted, so that
+    // c_max does not depend on the axis order
+    const float ma = fminf(fminf(fabsf(m0), fabsf(m1)), fabsf(m2));
+    const float mc = fmaxf(fmaxf(fabsf(m0), fabsf(m1)), fabsf(m2));
+    const float mb = fmaxf(fminf(fabsf(m0), fabsf(m1)), fminf(fmaxf(fabsf(m0), fabsf(m1)), fabsf(m2)));
+    const float ba = fminf(fminf(fabsf(b0), fabsf(b1)), fabsf(b2));
+    const float bc = fmaxf(fmaxf(fabsf(b0), fabsf(b1)), fabsf(b2));
+    const float bm = fmaxf(fminf(fabsf(b0), fabsf(b1)), fminf(fmaxf(fabsf(b0), fabsf(b1)), fabsf(b2)));
+    p = pressure_comp(rho, __fdividef(1.f, rho), ma, mb, mc, E, ba, bm, bc, gamma - T(1));
+  } else if (PM == PM_FP64) {
     const double rd = rho, mm0 = m0, mm1 = m1, mm2 = m2, c0 = b0, c1 = b1, c2 = b2;
     const double ke = 0.5 * (mm0 * mm0 + mm1 * mm1 + mm2 * mm2) / rd;
     p = (T)(((double)gamma - 1.0) * ((double)E - ke - 0.5 * (c0 * c0 + c1 * c1 + c2 * c2)));
@@ -288,7 +350,7 @@ __host__ __device__ constexpr int axis_t2(int a) { return (a + 2) % 3; }
 // ------------------------------------------------------------------------------------
 
 // CFL speed of cell i of a state, with B averaged from the faces to the cell centre
-template <typename T, bool P64>
+template <typename T, int PM>
 __device__ __forceinline__ T cmax_cell(const GridDesc& g, const FieldSet<T>& in, long long i,
                                        T gamma, int* st) {
   const int z = (int)(i % g.n[2]);
@@ -302,12 +364,12 @@ __device__ __forceinline__ T cmax_cell(const GridDesc& g, const FieldSet<T>& in,
     const long long gn = i + (long long)(wrap_index(c[a] + 1, g.n[a], g.bc[a]) - c[a]) * g.s[a];
     bc[a] = T(0.5) * (in.f[5 + a][i] + in.f[5 + a][gn]);
   }
-  return cell_cmax<T, P64>(in.f[0][i], in.f[1][i], in.f[2][i], in.f[3][i], in.f[4][i], bc[0],
+  return cell_cmax<T, PM>(in.f[0][i], in.f[1][i], in.f[2][i], in.f[3][i], in.f[4][i], bc[0],
                            bc[1], bc[2], gamma, st);
 }
 
 // c_max of cells [i0, i1) by one block, folded into the partial maxima of ds
-template <typename T, bool P64>
+template <typename T, int PM>
 __device__ __forceinline__ void cmax_range(const GridDesc& g, const FieldSet<T>& in, T gamma,
                                            DevScalars* ds, long long i0, long long i1,
                                            long long stride) {
@@ -315,7 +377,7 @@ __device__ __forceinline__ void cmax_range(const GridDesc& g, const FieldSet<T>&
   bool nan_seen = false;
   int st = 0;
   for (long long i = i0; i < i1; i += stride) {
-    const T v = cmax_cell<T, P64>(g, in, i, gamma, &st);
+    const T v = cmax_cell<T, PM>(g, in, i, gamma, &st);
     if (v != v) nan_seen = true; else cm = fmax(cm, v);
   }
   block_max_to_global(cm, nan_seen, ds);
@@ -324,10 +386,10 @@ __device__ __forceinline__ void cmax_range(const GridDesc& g, const FieldSet<T>&
 
 // c_max of a state (at initialisation, on request, and at the end of a step whose last
 // fluid sweep runs along an axis of one cell)
-template <typename T, bool P64>
+template <typename T, int PM>
 __global__ void cmax_kernel(GridDesc g, FieldSet<T> in, T gamma, DevScalars* ds) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-  cmax_range<T, P64>(g, in, gamma, ds, blockIdx.x * (long long)blockDim.x + threadIdx.x, N,
+  cmax_range<T, PM>(g, in, gamma, ds, blockIdx.x * (long long)blockDim.x + threadIdx.x, N,
                      (long long)gridDim.x * blockDim.x);
 }
 

@@ -17,12 +17,12 @@ struct Launch {
   // fluid_axis(dt) with dt read from ds; last: also accumulate c_max of the result
   static cudaError_t fluid(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                            double gamma, double h, DevScalars* ds, int axis, bool last,
-                           bool p64, cudaStream_t s);
+                           int pm, cudaStream_t s);
   // CT along axis for both transverse components (t1 then t2)
   static cudaError_t ct(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                         double h, DevScalars* ds, int axis, cudaStream_t s);
   static cudaError_t cmax(const GridDesc& g, const FieldSet<T>& in, double gamma,
-                          DevScalars* ds, bool p64, cudaStream_t s);
+                          DevScalars* ds, int pm, cudaStream_t s);
   static cudaError_t dt(DevScalars* ds, double cfl_h, cudaStream_t s);
   static cudaError_t sums(long long n, const FieldSet<T>& in, double* partial, int nblocks,
                           double* out, cudaStream_t s);

@@ -21,14 +21,14 @@ constexpr int kSegWarps = 4;
 #endif
 template <typename T> struct SegK { static constexpr int K = sizeof(T) == 4 ? MHD_SEG_K_F32 : 2; };
 
-template <typename T, int A, bool LAST, bool P64>
+template <typename T, int A, bool LAST, int PM>
 static cudaError_t set_march_attr() {
   cudaError_t e = cudaFuncSetAttribute(
-      fluid_march_xy<T, A, LAST, P64, MarchCfg<T>::S, MarchCfg<T>::NT>,
+      fluid_march_xy<T, A, LAST, PM, MarchCfg<T>::S, MarchCfg<T>::NT>,
       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
   if constexpr (sizeof(T) == 4) {
     const cudaError_t e2 = cudaFuncSetAttribute(
-        fluid_march_xy_vec<A, LAST, P64, MarchCfg<T>::S, MarchCfg<T>::NT>,
+        fluid_march_xy_vec<A, LAST, PM, MarchCfg<T>::S, MarchCfg<T>::NT>,
         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
     if (e2 != cudaSuccess) e = e2;
   }
@@ -51,19 +51,19 @@ static cudaError_t set_ct_rows_attr() {
                               (int)ct_rows_smem<T>(kRowsR));
 }
 
-template <typename T, bool P64>
+template <typename T, int PM>
 static cudaError_t setup_p() {
   cudaError_t e = cudaSuccess;
 #define MHD_TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) e = _e; } while (0)
-  MHD_TRY((set_march_attr<T, 0, false, P64>()));
-  MHD_TRY((set_march_attr<T, 1, false, P64>()));
-  MHD_TRY((set_march_attr<T, 0, true, P64>()));
-  MHD_TRY((set_march_attr<T, 1, true, P64>()));
+  MHD_TRY((set_march_attr<T, 0, false, PM>()));
+  MHD_TRY((set_march_attr<T, 1, false, PM>()));
+  MHD_TRY((set_march_attr<T, 0, true, PM>()));
+  MHD_TRY((set_march_attr<T, 1, true, PM>()));
 #undef MHD_TRY
   return e;
 }
 
-template <typename T, bool LAST, bool P64>
+template <typename T, bool LAST, int PM>
 static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                            T gamma, double h, DevScalars* ds, int axis, cudaStream_t s) {
   constexpr int S = MarchCfg<T>::S, NT = MarchCfg<T>::NT;
@@ -74,46 +74,53 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
     const size_t sm = march_tile_smem<T>();
     if constexpr (sizeof(T) == 4) {
       if (march_vec<T>(g)) {
-        if (axis == 0) fluid_march_xy_vec<0, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
-        else fluid_march_xy_vec<1, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        if (axis == 0) fluid_march_xy_vec<0, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        else fluid_march_xy_vec<1, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
         return;
       }
     }
-    if (axis == 0) fluid_march_xy<T, 0, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
-    else fluid_march_xy<T, 1, LAST, P64, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+    if (axis == 0) fluid_march_xy<T, 0, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+    else fluid_march_xy<T, 1, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
     return;
   }
   if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
     constexpr int K = 2, SEG = 32 * K - 6;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
-    fluid_seg_z<T, LAST, P64, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
+    fluid_seg_z<T, LAST, PM, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
                                               32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
     return;
   }
   constexpr int K = SegK<T>::K, SEG = 32 * K - 6;
   const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
-  fluid_seg_z<T, LAST, P64, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
+  fluid_seg_z<T, LAST, PM, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
                                             32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
 }
 
 template <typename T>
 static cudaError_t cmax_impl(const GridDesc& g, const FieldSet<T>& in, double gamma,
-                             DevScalars* ds, bool p64, cudaStream_t s);
+                             DevScalars* ds, int pm, cudaStream_t s);
 
 template <typename T>
 static cudaError_t fluid_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                               double gamma, double h, DevScalars* ds, int axis, bool last,
-                              bool p64, cudaStream_t s) {
+                              int pm, cudaStream_t s) {
   if (axis_is_flat(g, axis))   // identity (mhd_flat.cuh); the caller does not swap buffers
-    return last ? cmax_impl<T>(g, in, gamma, ds, p64, s) : cudaSuccess;
+    return last ? cmax_impl<T>(g, in, gamma, ds, pm, s) : cudaSuccess;
   const T gm = (T)gamma;
-  if (last) {
-    if (p64) fluid_dispatch<T, true, true>(g, in, out, gm, h, ds, axis, s);
-    else fluid_dispatch<T, true, false>(g, in, out, gm, h, ds, axis, s);
-  } else {
-    if (p64) fluid_dispatch<T, false, true>(g, in, out, gm, h, ds, axis, s);
-    else fluid_dispatch<T, false, false>(g, in, out, gm, h, ds, axis, s);
+  if constexpr (sizeof(T) == 4) {
+    if (pm == PM_FP64) {
+      if (last) fluid_dispatch<T, true, PM_FP64>(g, in, out, gm, h, ds, axis, s);
+      else fluid_dispatch<T, false, PM_FP64>(g, in, out, gm, h, ds, axis, s);
+      return cudaGetLastError();
+    }
+    if (pm == PM_COMP) {
+      if (last) fluid_dispatch<T, true, PM_COMP>(g, in, out, gm, h, ds, axis, s);
+      else fluid_dispatch<T, false, PM_COMP>(g, in, out, gm, h, ds, axis, s);
+      return cudaGetLastError();
+    }
   }
+  if (last) fluid_dispatch<T, true, PM_FP32>(g, in, out, gm, h, ds, axis, s);
+  else fluid_dispatch<T, false, PM_FP32>(g, in, out, gm, h, ds, axis, s);
   return cudaGetLastError();
 }
 
@@ -167,12 +174,16 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
 
 template <typename T>
 static cudaError_t cmax_impl(const GridDesc& g, const FieldSet<T>& in, double gamma,
-                             DevScalars* ds, bool p64, cudaStream_t s) {
+                             DevScalars* ds, int pm, cudaStream_t s) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   long long nb = (N + 255) / 256;
   if (nb > 152 * 16) nb = 152 * 16;
-  if (p64) cmax_kernel<T, true><<<(unsigned)nb, 256, 0, s>>>(g, in, (T)gamma, ds);
-  else cmax_kernel<T, false><<<(unsigned)nb, 256, 0, s>>>(g, in, (T)gamma, ds);
+  if (sizeof(T) == 4 && pm == PM_FP64)
+    cmax_kernel<T, PM_FP64><<<(unsigned)nb, 256, 0, s>>>(g, in, (T)gamma, ds);
+  else if (sizeof(T) == 4 && pm == PM_COMP)
+    cmax_kernel<T, PM_COMP><<<(unsigned)nb, 256, 0, s>>>(g, in, (T)gamma, ds);
+  else
+    cmax_kernel<T, PM_FP32><<<(unsigned)nb, 256, 0, s>>>(g, in, (T)gamma, ds);
   return cudaGetLastError();
 }
 
@@ -187,8 +198,11 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
 
 #define MHD_INSTANTIATE_LAUNCH(T)                                                            \
   template <> cudaError_t Launch<T>::setup() {                                              \
-    cudaError_t e = setup_p<T, false>();                                                    \
-    if (sizeof(T) == 4) { cudaError_t e2 = setup_p<T, true>(); if (e2 != cudaSuccess) e = e2; } \
+    cudaError_t e = setup_p<T, PM_FP32>();                                                  \
+    if (sizeof(T) == 4) {                                                                   \
+      cudaError_t e2 = setup_p<T, PM_FP64>(); if (e2 != cudaSuccess) e = e2;                \
+      e2 = setup_p<T, PM_COMP>(); if (e2 != cudaSuccess) e = e2;                            \
+    }                                                                                       \
     cudaError_t e3 = set_ct_march_attr<T, 0>(); if (e3 != cudaSuccess) e = e3;              \
     e3 = set_ct_march_attr<T, 1>(); if (e3 != cudaSuccess) e = e3;                          \
     e3 = set_ct_rows_attr<T, 0>(); if (e3 != cudaSuccess) e = e3;                           \
@@ -197,16 +211,16 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
   }                                                                                         \
   template <> cudaError_t Launch<T>::fluid(const GridDesc& g, const FieldSet<T>& in,        \
       const FieldSet<T>& out, double gamma, double h, DevScalars* ds, int axis, bool last,  \
-      bool p64, cudaStream_t s) {                                                           \
-    return fluid_impl<T>(g, in, out, gamma, h, ds, axis, last, p64, s);                     \
+      int pm, cudaStream_t s) {                                                           \
+    return fluid_impl<T>(g, in, out, gamma, h, ds, axis, last, pm, s);                     \
   }                                                                                         \
   template <> cudaError_t Launch<T>::ct(const GridDesc& g, const FieldSet<T>& in,           \
       const FieldSet<T>& out, double h, DevScalars* ds, int axis, cudaStream_t s) {         \
     return ct_impl<T>(g, in, out, h, ds, axis, s);                                          \
   }                                                                                         \
   template <> cudaError_t Launch<T>::cmax(const GridDesc& g, const FieldSet<T>& in,         \
-      double gamma, DevScalars* ds, bool p64, cudaStream_t s) {                             \
-    return cmax_impl<T>(g, in, gamma, ds, p64, s);                                          \
+      double gamma, DevScalars* ds, int pm, cudaStream_t s) {                             \
+    return cmax_impl<T>(g, in, gamma, ds, pm, s);                                          \
   }                                                                                         \
   template <> cudaError_t Launch<T>::dt(DevScalars* ds, double cfl_h, cudaStream_t s) {     \
     dt_kernel<T><<<1, 1, 0, s>>>(ds, cfl_h);                                                \

@@ -20,7 +20,7 @@
 
 namespace mhd {
 
-template <typename T, bool P64, bool LAST>
+template <typename T, int PM, bool LAST>
 struct FluidPencil {
   T u1[5], u2[5], u3[5];   // u(j-1), u(j-2), u(j-3)
   T b1[3], b2[3], b3[3];   // cell-centred B at j-1, j-2, j-3
@@ -48,7 +48,7 @@ struct FluidPencil {
   __device__ __forceinline__ bool push(int k, const T u0[5], const T b0[3], T gamma, T dth,
                                        T hd, T out[5], T bout[3]) {
     T fr0[5], fl0[5];
-    st |= cell_flux<T, P64>(u0, b0, gamma, fr0, fl0);
+    st |= cell_flux<T, PM>(u0, b0, gamma, fr0, fl0);
     T uh[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -58,7 +58,7 @@ struct FluidPencil {
       fr1[c] = fr0[c];
     }
     T fr2[5], fl2[5];
-    const int s2 = cell_flux<T, P64>(uh, b1, gamma, fr2, fl2);
+    const int s2 = cell_flux<T, PM>(uh, b1, gamma, fr2, fl2);
     if (k >= 2) st |= s2;
     T g2c[5];
 #pragma unroll
@@ -167,7 +167,7 @@ constexpr int kCtUnroll = MHD_CT_UNROLL;
 // ------------------------------------------------------------------------------------
 // one tile: pencils bx*NT .. bx*NT+NT-1 of the transverse plane, cells by*S .. by*S+S-1
 // along the sweep; smem_raw holds the prefetch ring (march_ring_bytes)
-template <typename T, int A, bool LAST, bool P64, int S, int NT>
+template <typename T, int A, bool LAST, int PM, int S, int NT>
 __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, const FieldSet<T>& in,
                                                          const FieldSet<T>& out, T gamma, double h,
                                                          DevScalars* ds, unsigned bx, unsigned by,
@@ -201,7 +201,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, cons
   const T* __restrict__ bt2 = in.f[5 + T2];
   const long long sA = g.s[A];
 
-  FluidPencil<T, P64, LAST> P;
+  FluidPencil<T, PM, LAST> P;
   P.init();
   const int js = a0 - 3;
   const int kend = min(S, nA - a0) + 6;       // iterations needed for this tile
@@ -259,7 +259,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, cons
         out.f[4][co] = un[4];
         if (!(un[0] > T(0))) P.st |= ST_UNPHYSICAL;
         if (LAST) {
-          const T v = cell_cmax<T, P64>(un[0], un[1], un[2], un[3], un[4], bo[0], bo[1], bo[2],
+          const T v = cell_cmax<T, PM>(un[0], un[1], un[2], un[3], un[4], bo[0], bo[1], bo[2],
                                         gamma, &P.st);
           if (v != v) nan_seen = true; else cm = fmax(cm, v);
         }
@@ -288,7 +288,7 @@ __device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-template <int A, bool LAST, bool P64, int S, int NT>
+template <int A, bool LAST, int PM, int S, int NT>
 __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const FieldSet<float>& in,
                                                         const FieldSet<float>& out, float gamma,
                                                         double h, DevScalars* ds, unsigned bx,
@@ -347,7 +347,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
   };
 #pragma unroll
   for (int d = 0; d < kMarchDepth; ++d) issue(d);
-  FluidPencil<T, P64, LAST> P;
+  FluidPencil<T, PM, LAST> P;
   P.init();
   const long long base = (long long)z + (long long)o * sO;
   T bn_cur = in.f[5 + A][base + wrap_off<T>(js, nA, bcA, sA)];
@@ -384,7 +384,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
         out.f[4][co] = un[4];
         if (!(un[0] > T(0))) P.st |= ST_UNPHYSICAL;
         if (LAST) {
-          const T v = cell_cmax<T, P64>(un[0], un[1], un[2], un[3], un[4], bo[0], bo[1], bo[2],
+          const T v = cell_cmax<T, PM>(un[0], un[1], un[2], un[3], un[4], bo[0], bo[1], bo[2],
                                         gamma, &P.st);
           if (v != v) nan_seen = true; else cm = fmax(cm, v);
         }
@@ -407,25 +407,25 @@ static size_t march_tile_smem() {
   return sizeof(T) * (size_t)kMarchRing * kVecRows * 128;   // both stagings: 10 values per cell
 }
 
-template <typename T, int A, bool LAST, bool P64, int S, int NT>
+template <typename T, int A, bool LAST, int PM, int S, int NT>
 __device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const FieldSet<T>& in,
                                                     const FieldSet<T>& out, T gamma, double h,
                                                     DevScalars* ds, unsigned bx, unsigned by,
                                                     unsigned char* smem_raw) {
   if constexpr (sizeof(T) == 4 && NT == 128) {
     if (march_vec<T>(g)) {
-      fluid_march_xy_tile_vec<A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, bx, by, smem_raw);
+      fluid_march_xy_tile_vec<A, LAST, PM, S, NT>(g, in, out, gamma, h, ds, bx, by, smem_raw);
       return;
     }
   }
-  fluid_march_xy_tile_elem<T, A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, bx, by, smem_raw);
+  fluid_march_xy_tile_elem<T, A, LAST, PM, S, NT>(g, in, out, gamma, h, ds, bx, by, smem_raw);
 }
 
-template <typename T, int A, bool LAST, bool P64, int S, int NT>
+template <typename T, int A, bool LAST, int PM, int S, int NT>
 __global__ void __launch_bounds__(NT, MHD_MARCH_MINB)
 fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fluid_march_xy_tile_elem<T, A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, blockIdx.x,
+  fluid_march_xy_tile_elem<T, A, LAST, PM, S, NT>(g, in, out, gamma, h, ds, blockIdx.x,
                                                    blockIdx.y, smem_raw);
 }
 
@@ -434,12 +434,12 @@ fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, D
 #ifndef MHD_VEC_MINB
 #define MHD_VEC_MINB 4
 #endif
-template <int A, bool LAST, bool P64, int S, int NT>
+template <int A, bool LAST, int PM, int S, int NT>
 __global__ void __launch_bounds__(NT, MHD_VEC_MINB)
 fluid_march_xy_vec(GridDesc g, FieldSet<float> in, FieldSet<float> out, float gamma, double h,
                    DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fluid_march_xy_tile_vec<A, LAST, P64, S, NT>(g, in, out, gamma, h, ds, blockIdx.x, blockIdx.y,
+  fluid_march_xy_tile_vec<A, LAST, PM, S, NT>(g, in, out, gamma, h, ds, blockIdx.x, blockIdx.y,
                                                smem_raw);
 }
 
@@ -766,7 +766,8 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
   constexpr bool Z1 = (T1 == 2);             // the t1 pipeline runs across z (y sweep)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nzc = (g.n[2] + 30) / 31;
-  const int zr = (int)(bx % nzc) * 31 + lane;
+  const int z0 = (int)(bx % nzc) * 31;
+  const int zr = z0 + lane;
   const int orow = (int)(bx / nzc) * (R - 1) + w;
   const int zc = wrap_index(zr, g.n[2], g.bc[2]);
   const int oc = wrap_index(orow, g.n[O], g.bc[O]);
@@ -777,8 +778,9 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
   const T dth = (T)(ds->dt / h);
   const T hd = T(0.5) * dth;
   const long long base = (long long)zc + (long long)oc * g.s[O];
+  const int oc_lo = wrap_index(oc - 1, g.n[O], g.bc[O]);
   const long long lo_z = (long long)(wrap_index(zc - 1, g.n[2], g.bc[2]) - zc);
-  const long long lo_o = (long long)(wrap_index(oc - 1, g.n[O], g.bc[O]) - oc) * g.s[O];
+  const long long lo_o = (long long)(oc_lo - oc) * g.s[O];
   const long long lo1 = Z1 ? lo_z : lo_o, lo2 = Z1 ? lo_o : lo_z;
   const T* __restrict__ pr = in.f[0];
   const T* __restrict__ pm = in.f[1 + A];
@@ -799,47 +801,23 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
   const int kend = min(S, nA - a0) + 8;
   T* ring = reinterpret_cast<T*>(smem_raw);
   T* xbuf = ring + (size_t)kMarchRing * 9 * NT;   // [2][NT] EMF of the O pipeline
-  constexpr int NV = 9;
-  auto issue = [&](int kk) {
-    if (kk < kend) {
-      const long long c = base + (long long)wrap_index(js + kk, nA, bcA) * sA;
-      T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
-      cp_async_elem(slot + 0 * NT, pr + c);
-      cp_async_elem(slot + 1 * NT, pr + c + lo1);
-      cp_async_elem(slot + 2 * NT, pr + c + lo2);
-      cp_async_elem(slot + 3 * NT, pm + c);
-      cp_async_elem(slot + 4 * NT, pm + c + lo1);
-      cp_async_elem(slot + 5 * NT, pm + c + lo2);
-      cp_async_elem(slot + 6 * NT, pb1 + c);
-      cp_async_elem(slot + 7 * NT, pb2 + c);
-      cp_async_elem(slot + 8 * NT, pba + c);
-    }
-    cp_async_commit();
-  };
-#pragma unroll
-  for (int d = 0; d < kMarchDepth; ++d) issue(d);
   int st = 0;
-#pragma unroll kCtUnroll
-  for (int k = 0; k < kend; ++k) {
-    issue(k + kMarchDepth);
-    cp_async_wait<kMarchDepth>();
-    const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+  // one cell of the march: face velocities, both EMF pipelines, the EMF exchange and the
+  // constraint on B_A; r = rho (own, lo1, lo2), m = m_A (same), b1, b2, ba the face fields
+  auto cell = [&](int k, T r0, T r1, T r2, T m0, T m1, T m2, T b1in, T b2in, T bain) {
     const int j = js + k;
-    const T r0 = slot[0], r1 = slot[1 * NT], r2 = slot[2 * NT];
-    const T m0 = slot[3 * NT], m1 = slot[4 * NT], m2 = slot[5 * NT];
     const T vf1 = Num<T>::div(m0 + m1, r0 + r1);     // face velocities below the pencil
     const T vf2 = Num<T>::div(m0 + m2, r0 + r2);
     T bt1 = T(0), bt2 = T(0), e1 = T(0), e2 = T(0);
     if constexpr (PACK) {
       float2 e12;
       const float2 bt = pp2.push(make_float2((float)vf1, (float)vf2),
-                                 make_float2((float)slot[6 * NT], (float)slot[7 * NT]), ndth2,
-                                 nhd2, &e12);
+                                 make_float2((float)b1in, (float)b2in), ndth2, nhd2, &e12);
       bt1 = bt.x; bt2 = bt.y; e1 = e12.x; e2 = e12.y;
     } else {
       // the halo row only feeds the O pipeline's EMF to the row below
-      if (!halo_row || !Z1) bt1 = p1.push(vf1, slot[6 * NT], dth, hd, &e1);
-      if (!halo_row || Z1) bt2 = p2.push(vf2, slot[7 * NT], dth, hd, &e2);
+      if (!halo_row || !Z1) bt1 = p1.push(vf1, b1in, dth, hd, &e1);
+      if (!halo_row || Z1) bt2 = p2.push(vf2, b2in, dth, hd, &e2);
     }
     const T eo = Z1 ? e2 : e1;                       // EMF of the O pipeline
     T* xb = xbuf + (k & 1) * NT;
@@ -857,13 +835,95 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
     const T en1 = Z1 ? ez_up : eo_up, en2 = Z1 ? eo_up : ez_up;
     T b = ffma(dc, en1 - e1, ba4);           // constraint from t1, then t2
     b = ffma(dc, en2 - e2, b);
-    ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = slot[8 * NT];
+    ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = bain;
     if (k >= 8 && out_ok) {
       const long long co = base + (long long)(j - 4) * sA;
       out.f[5 + T1][co] = bt1;
       out.f[5 + T2][co] = bt2;
       out.f[5 + A][co] = b;
       if (!(bt1 == bt1) || !(bt2 == bt2) || !(b == b)) st |= ST_NONFINITE;
+    }
+  };
+  // 16-byte staging (FP32, nz a multiple of 4, a z chunk that needs no wrap): each warp
+  // copies, per cell, 7 rows of the 36 aligned z positions around its 32 pencils (rho, m_A
+  // of its own row and of the row below across O, B_t1, B_t2, B_A), 9 groups of 4 each:
+  // two 16-byte copies per lane instead of 9 single values; the z - 1 neighbours of rho and
+  // m_A are the row's previous positions.  Lanes read each other's copies after their own
+  // wait and a warp barrier.
+  // staged z range [zb, zb + 36): aligned, holding z0 - 1 .. z0 + 31, inside the row
+  const int zb = (z0 - 1) & ~3;
+  bool vec = false;
+  if constexpr (sizeof(T) == 4) vec = g.n[2] % 4 == 0 && z0 >= 1 && zb + 36 <= g.n[2];
+  if (vec) {
+    constexpr int VW = 36, VR = 7;           // values per row, rows per cell
+    const int zo = z0 - zb;                  // this warp's first pencil in the row (1..4)
+    float* wring = reinterpret_cast<float*>(smem_raw) + (size_t)w * kMarchRing * VR * VW;
+    // this lane's copies: c = lane and lane + 32 of the 63 (row c / 9, group c % 9)
+    const float* src[2];
+    int dst[2];
+    bool has[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c = lane + 32 * q;
+      has[q] = c < VR * 9;
+      const int row = has[q] ? c / 9 : 0, grp = c % 9;
+      const float* f = (const float*)(row == 0 || row == 2 ? in.f[0] : row == 1 || row == 3
+                                      ? in.f[1 + A] : row == 4 ? in.f[5 + T1] : row == 5
+                                      ? in.f[5 + T2] : in.f[5 + A]);
+      const int orow_c = (row == 2 || row == 3) ? oc_lo : oc;
+      src[q] = f + (long long)orow_c * g.s[O] + zb + 4 * grp;
+      dst[q] = row * VW + 4 * grp;
+    }
+    auto issue = [&](int kk) {
+      if (kk < kend) {
+        const long long off = (long long)wrap_index(js + kk, nA, bcA) * sA;
+        float* slot = wring + (size_t)(kk % kMarchRing) * VR * VW;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+          if (has[q]) cp_async_16(slot + dst[q], src[q] + off);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int d = 0; d < kMarchDepth; ++d) issue(d);
+    const int own = zo + lane, lz = own - 1;
+    const int l1 = Z1 ? lz : 2 * VW + own, l2 = Z1 ? 2 * VW + own : lz;   // lo1, lo2 of rho
+#pragma unroll kCtUnroll
+    for (int k = 0; k < kend; ++k) {
+      cp_async_wait<kMarchDepth - 1>();
+      __syncwarp();
+      issue(k + kMarchDepth);
+      const float* sl = wring + (size_t)(k % kMarchRing) * VR * VW;
+      cell(k, (T)sl[own], (T)sl[l1], (T)sl[l2], (T)sl[VW + own], (T)sl[VW + l1],
+           (T)sl[VW + l2], (T)sl[4 * VW + own], (T)sl[5 * VW + own], (T)sl[6 * VW + own]);
+    }
+  } else {
+    constexpr int NV = 9;
+    auto issue = [&](int kk) {
+      if (kk < kend) {
+        const long long c = base + (long long)wrap_index(js + kk, nA, bcA) * sA;
+        T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
+        cp_async_elem(slot + 0 * NT, pr + c);
+        cp_async_elem(slot + 1 * NT, pr + c + lo1);
+        cp_async_elem(slot + 2 * NT, pr + c + lo2);
+        cp_async_elem(slot + 3 * NT, pm + c);
+        cp_async_elem(slot + 4 * NT, pm + c + lo1);
+        cp_async_elem(slot + 5 * NT, pm + c + lo2);
+        cp_async_elem(slot + 6 * NT, pb1 + c);
+        cp_async_elem(slot + 7 * NT, pb2 + c);
+        cp_async_elem(slot + 8 * NT, pba + c);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int d = 0; d < kMarchDepth; ++d) issue(d);
+#pragma unroll kCtUnroll
+    for (int k = 0; k < kend; ++k) {
+      issue(k + kMarchDepth);
+      cp_async_wait<kMarchDepth>();
+      const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+      cell(k, slot[0], slot[1 * NT], slot[2 * NT], slot[3 * NT], slot[4 * NT], slot[5 * NT],
+           slot[6 * NT], slot[7 * NT], slot[8 * NT]);
     }
   }
   cp_async_wait<0>();

@@ -141,7 +141,7 @@ __device__ __forceinline__ void seg_stage2(const V (&fr2)[K], const V (&fl2)[K],
 }
 
 // one warp: window `wid` (seg_place); all 32 lanes call it
-template <typename T, bool LAST, bool P64, int K, bool NC>
+template <typename T, bool LAST, int PM, int K, bool NC>
 __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                                  const FieldSet<T>& out, T gamma, double h,
                                                  DevScalars* ds, long long wid) {
@@ -179,7 +179,7 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       T a[5], c[5];
-      st |= cell_flux<T, P64>(u[i], b[i], gamma, a, c);
+      st |= cell_flux<T, PM>(u[i], b[i], gamma, a, c);
 #pragma unroll
       for (int q = 0; q < 5; ++q) { fr[q][i] = a[q]; fl[q][i] = c[q]; }
     }
@@ -202,7 +202,7 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       T a[5], c[5];
-      const int s2 = cell_flux<T, P64>(uh[i], b[i], gamma, a, c);
+      const int s2 = cell_flux<T, PM>(uh[i], b[i], gamma, a, c);
       const int w = lane * K + i;                          // window cell, 1 .. 32K-2 valid
       if (w >= 1 && w <= 32 * K - 2) st |= s2;
 #pragma unroll
@@ -234,7 +234,7 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
       out.f[4][co] = un[i][4];
       if (!(un[i][0] > T(0))) st |= ST_UNPHYSICAL;
       if (LAST) {
-        const T v = cell_cmax<T, P64>(un[i][0], un[i][1], un[i][2], un[i][3], un[i][4], b[i][0],
+        const T v = cell_cmax<T, PM>(un[i][0], un[i][1], un[i][2], un[i][3], un[i][4], b[i][0],
                                       b[i][1], b[i][2], gamma, &st);
         if (v != v) nan_seen = true; else cm = fmax(cm, v);
       }
@@ -258,10 +258,10 @@ template <typename T> struct SegMinBlocks {
   static constexpr int fluid = sizeof(T) == 4 ? MHD_SEG_MINB : 0;
   static constexpr int ct = sizeof(T) == 4 ? MHD_CTSEG_MINB : 0;
 };
-template <typename T, bool LAST, bool P64, int NW, int K>
+template <typename T, bool LAST, int PM, int NW, int K>
 __global__ void __launch_bounds__(32 * NW, SegMinBlocks<T>::fluid)
 fluid_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
-  fluid_seg_z_warp<T, LAST, P64, K, true>(g, in, out, gamma, h, ds,
+  fluid_seg_z_warp<T, LAST, PM, K, true>(g, in, out, gamma, h, ds,
                                           (long long)blockIdx.x * NW + (threadIdx.x >> 5));
 }
 

@@ -19,6 +19,7 @@ LIB_PATH = _build.LIB
 MHD_OK, MHD_ERR_INVALID, MHD_ERR_OOM, MHD_ERR_CUDA, MHD_ERR_UNPHYSICAL, MHD_ERR_TIMEOUT = range(6)
 PERIODIC, OUTFLOW = 0, 1
 FP32, FP64 = 0, 1
+PRESSURE_FP32, PRESSURE_FP64, PRESSURE_COMPENSATED = 0, 1, 2   # mhd_pressure_mode
 
 # every symbol include/mhd.h declares; tests check the library exports them all
 EXPORTS = ("mhd_create", "mhd_init_fields", "mhd_upload", "mhd_step", "mhd_apply", "mhd_cmax",
@@ -106,10 +107,14 @@ class Solver:
     """One grid on the GPU (mhd_create ... mhd_destroy)."""
 
     def __init__(self, n, bc=(PERIODIC,) * 3, h=1.0, gamma=5.0 / 3.0, cfl=0.7, prec=FP32,
-                 fp64_pressure=False, stream=None):
+                 fp64_pressure=False, stream=None, pressure=None):
+        """pressure: PRESSURE_FP32 / PRESSURE_FP64 / PRESSURE_COMPENSATED (mhd_pressure_mode);
+        fp64_pressure=True is PRESSURE_FP64."""
         self.lib = load_library()
+        pm = int(pressure) if pressure is not None else (PRESSURE_FP64 if fp64_pressure
+                                                         else PRESSURE_FP32)
         cfg = MhdConfig(int(n[0]), int(n[1]), int(n[2]), float(h), float(gamma), float(cfl),
-                        (C.c_int * 3)(*[int(b) for b in bc]), int(prec), int(bool(fp64_pressure)),
+                        (C.c_int * 3)(*[int(b) for b in bc]), int(prec), pm,
                         C.c_void_p(stream if stream else None))
         h_ = C.c_void_p()
         st = self.lib.mhd_create(C.byref(cfg), C.byref(h_))

@@ -240,23 +240,90 @@ def test_determinism_and_checkpoint(mhd):
     assert np.array_equal(a, b)
 
 
-def test_fp64_pressure_flag(mhd):
-    """FP32 sweeps with the pressure recovered in FP64: within the FP32 tolerance of the
-    oracle like plain FP32, and not the plain FP32 result (the flag selects the FP64
-    recovery)."""
-    prob = I.batched_instance(0)
-    ref = oracle.Oracle.from_problem(prob)
-    ref.step(5)
-    errs, got = [], []
-    for flag in (False, True):
+def test_pressure_modes_low_beta(mhd):
+    """The FP32 sweeps with each pressure recovery (plain FP32, FP64, compensated FP32) on
+    the lowest-beta instance of the batched workload (beta = 0.126): all within the FP32
+    tolerance of the FP64 oracle run from the same (FP32) input after 10 steps; the FP64 and
+    compensated recoveries give nearly the same state, and not plain FP32's."""
+    prob = I.batched_instance(52)
+    f32 = prob.fields.astype(np.float32)
+    ref = oracle.Oracle(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, f32.astype(np.float64))
+    ref.step(10)
+    got, errs = {}, {}
+    for pm in (mhd.PRESSURE_FP32, mhd.PRESSURE_FP64, mhd.PRESSURE_COMPENSATED):
         with mhd.Solver(prob.n, prob.bc, prob.h, prob.gamma, prob.cfl, prec=mhd.FP32,
-                        fp64_pressure=flag) as s:
-            s.init_fields(prob.fields)
-            s.step(5, sync=True)
-            got.append(s.read())
-            errs.append(rel_l1(got[-1], ref.f))
-    assert np.all(errs[0] <= FP32_TOL) and np.all(errs[1] <= FP32_TOL)
-    assert not np.array_equal(got[0], got[1])
+                        pressure=pm) as s:
+            s.upload([f32[k] for k in range(8)])
+            s.step(10, sync=True)
+            got[pm] = s.read()
+        errs[pm] = rel_l1(got[pm], ref.f)
+        assert np.all(errs[pm] <= FP32_TOL), (pm, errs[pm])
+    d_comp = rel_l1(got[mhd.PRESSURE_COMPENSATED], got[mhd.PRESSURE_FP64]).max()
+    d_plain = rel_l1(got[mhd.PRESSURE_FP32], got[mhd.PRESSURE_FP64]).max()
+    assert not np.array_equal(got[mhd.PRESSURE_FP32], got[mhd.PRESSURE_FP64])
+    assert d_comp <= 0.25 * d_plain, (d_comp, d_plain)
+
+
+def hypersonic_state(shape, axis, seed=5, gamma=5.0 / 3.0):
+    """A hypersonic, unmagnetised FP32 state, constant along `axis` and random across it,
+    whose thermal energy is a few FP32 ulps of its total energy: per pencil |v| in [50, 100],
+    rho in [0.5, 2], B = 0, and E the first FP32 value above the kinetic energy of the
+    stored rho and m.  The exact pressure of the stored values is then positive and below
+    4e-8 of E.  Returns the (8, N) FP32 fields and that pressure per cell."""
+    rng = np.random.default_rng(seed)
+    cross = list(shape)
+    cross[axis] = 1
+    M = int(np.prod(cross))
+    rho = rng.uniform(0.5, 2.0, M).astype(np.float32)
+    d = rng.normal(size=(3, M))
+    d /= np.linalg.norm(d, axis=0)
+    m = (rho.astype(np.float64) * rng.uniform(50, 100, M) * d).astype(np.float32)
+    ke = 0.5 * (m.astype(np.float64) ** 2).sum(axis=0) / rho.astype(np.float64)
+    E = ke.astype(np.float32)
+    E = np.where(E.astype(np.float64) > ke, E, np.nextafter(E, np.float32(np.inf)))
+    f = np.zeros((8,) + tuple(cross), dtype=np.float32)
+    f[0], f[1:4], f[4] = rho.reshape(cross), m.reshape((3,) + tuple(cross)), E.reshape(cross)
+    f = np.ascontiguousarray(np.broadcast_to(f, (8,) + tuple(shape)).reshape(8, -1))
+    p_exact = (gamma - 1.0) * (f[4].astype(np.float64) - 0.5 * (f[1:4].astype(np.float64) ** 2)
+                               .sum(axis=0) / f[0].astype(np.float64))
+    assert p_exact.min() > 0
+    return f, p_exact
+
+
+def test_pressure_recovery_hypersonic(mhd):
+    """Where the pressure is below an ulp of E (kinetic energy ~1e8 times the thermal one),
+    plain FP32 recovery cancels to the wrong sign in some pencils (a negative sound-speed
+    radicand: MHD_ERR_UNPHYSICAL), while the FP64 and the compensated FP32 recoveries get the
+    exact pressure of the stored values.  The state is constant along the sweep axis, so a
+    fluid sweep must return it unchanged, bit for bit (the oracle does), and the CFL speed
+    must be that of the exact pressure."""
+    shape, h, gamma, dt = (24, 10, 12), 1.0 / 24, 5.0 / 3.0, 1e-6
+    for axis in range(3):
+        f, p_exact = hypersonic_state(shape, axis, seed=5 + axis)
+        f64 = f.astype(np.float64)
+        v = f64[1:4] / f64[0]
+        cs = np.sqrt(gamma * p_exact / f64[0])
+        cmax_exact = (np.abs(v).max(axis=0) + cs).max()
+        ref = oracle.Oracle(shape, (0, 0, 0), h, gamma, 0.5, f64)
+        ref.fluid(axis, dt)
+        assert ref.status == 0 and np.array_equal(ref.f, f64)
+        res, st, cm = {}, {}, {}
+        for pm in (mhd.PRESSURE_FP32, mhd.PRESSURE_FP64, mhd.PRESSURE_COMPENSATED):
+            with mhd.Solver(shape, (0, 0, 0), h, gamma, 0.5, prec=mhd.FP32, pressure=pm) as s:
+                st_up = s.lib.mhd_upload(s.ctx, mhd._ptrs8([f[k].ctypes.data for k in range(8)]),
+                                         0, 0, 0.0)
+                s.apply(0, axis, dt)
+                st[pm] = (st_up, s.sync(check=False))
+                out = np.empty_like(f)
+                s.download([out[k] for k in range(8)], check=False)
+                res[pm] = out
+                if pm != mhd.PRESSURE_FP32:
+                    cm[pm] = s.cmax()
+        assert st[mhd.PRESSURE_FP32][1] == mhd.MHD_ERR_UNPHYSICAL, st
+        for pm in (mhd.PRESSURE_FP64, mhd.PRESSURE_COMPENSATED):
+            assert st[pm] == (mhd.MHD_OK, mhd.MHD_OK), (axis, pm, st[pm])
+            assert np.array_equal(res[pm], f), (axis, pm)
+            assert abs(cm[pm] - cmax_exact) <= 1e-6 * cmax_exact, (axis, pm, cm[pm], cmax_exact)
 
 
 def test_fp32_sums_exact_widening(mhd):
