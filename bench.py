@@ -43,8 +43,8 @@ FALLBACK_HBM_GBS = 6800.0
 ALG_BYTES = {"fluid": 13 * 4, "ct": 8 * 4}
 STEP_ALG_BYTES = 384
 # DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
-# a step) from ncu captures on a 256^3 grid (profiles/sweep_kernels_blast256_fp32.md), keyed
-# by the hash of the kernel sources they were taken on; another hash reports null.
+# a step) from ncu captures on a 256^3 grid (the ncu summaries under profiles/), keyed by the
+# hash of the kernel sources they were taken on; another hash reports null.
 NCU_TRAFFIC_PER_CELL = {"5fc818fba809cbc8": 50.66}
 # thread instructions per cell of one launch of each sweep kernel (ncu
 # smsp__thread_inst_executed.sum / cells, 256^3, the variants that do not reduce c_max),
@@ -328,9 +328,8 @@ def run_ours(args, world, rank, local):
     solver.step(args.warmup, sync=True)
     solver.sums()
 
-    # ---- timed region: device-resident state, kernel-by-kernel with CUDA events ----
-    solver.profile(True)
-    solver.profile_read(reset=True)
+    # ---- timed region: device-resident state, steps as the product runs them (one CUDA
+    # graph per step), CUDA events on the context stream around the whole region ----
     stream = torch.cuda.ExternalStream(solver.stream_handle())
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dev_uuid = None
@@ -357,8 +356,20 @@ def run_ours(args, world, rank, local):
     barrier(world)
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
+    # ---- per-kernel times: the same steps launched kernel by kernel, an event pair around
+    # each launch (a second region after the timed one) ----
+    psteps = min(args.steps, 30)
+    solver.profile(True)
+    solver.profile_read(reset=True)
+    ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ep0.record(stream)
+    solver.step(psteps)
+    ep1.record(stream)
+    ep1.synchronize()
+    solver.sync()
     prof = solver.profile_read(reset=True)
     solver.profile(False)
+    prof_step_ms = ep0.elapsed_time(ep1) / psteps
     max_ms = max_over_ranks(ms_total, world)
     total_cells = sum_over_ranks(float(N) * args.steps, world)
     value = total_cells / (max_ms / 1e3)
@@ -378,7 +389,7 @@ def run_ours(args, world, rank, local):
     src_hash = kernel_source_hash()
     tpc = NCU_TRAFFIC_PER_CELL.get(src_hash)
     traffic = tpc * N if tpc is not None else None
-    launches = sum(c for _, c in prof.values()) + 2 * sums_calls
+    launches = sum(c for _, c in prof.values()) * args.steps // psteps + 2 * sums_calls
 
     # ---- e2e: through the C ABI with pinned host buffers, copies inside the region ----
     e2e = None
@@ -425,6 +436,10 @@ def run_ours(args, world, rank, local):
                                   "frac": STEP_ALG_BYTES * N / (step_ms / 1e3) / 1e9 / peak},
                 "issue": issue,
                 "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
+                "kernels_timing": {"steps": psteps, "ms_per_step": prof_step_ms,
+                                   "how": "kernel-by-kernel launches with an event pair "
+                                          "around each, after the timed region (which "
+                                          "replays one CUDA graph per step)"},
                 "gpu_launches": launches, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0

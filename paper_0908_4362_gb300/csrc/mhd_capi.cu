@@ -5,11 +5,12 @@
 // left by the previous step into dt (clipped to t_end) and advances t; then the forward
 // sweep applies, for the axis order (a, b, c) of the current phase, fluid_a, CT_a,
 // fluid_b, CT_b, fluid_c, CT_c, and the reverse sweep CT_c, fluid_c, CT_b, fluid_b, CT_a,
-// fluid_a (reverse L: magnetic updates first, Sect. 4.3).  The last fluid sweep also
-// reduces the next c_max.  Each sweep is out of place; the context tracks which of the two
-// buffers holds each field.  A step flips every field an even number of times, so the
-// launch sequence of a step depends only on the phase, and one CUDA graph per phase is
-// replayed.
+// fluid_a (reverse L: magnetic updates first, Sect. 4.3); where c is z, the two CT_z in the
+// middle run as one launch.  The last fluid sweep also reduces the next c_max.  Each sweep is
+// out of place; the context tracks which of the two buffers holds each field.  A step's
+// launch sequence depends on the phase and on the buffer state it starts from, which
+// alternates between two states (the middle CT_z pair flips the B buffers once), so each
+// phase keeps up to two captured CUDA graphs.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -108,6 +109,26 @@ static cudaError_t enqueue_ct(mhd_ctx* ctx, int axis) {
   return e;
 }
 
+// the middle CT_z pair of a step runs as one launch (MHD_PAIR_Z = 1) or as two (0)
+#ifndef MHD_PAIR_Z
+#define MHD_PAIR_Z 1
+#endif
+static constexpr bool kPairZ = MHD_PAIR_Z != 0;
+
+// CT along z twice (one launch, the same bits as two enqueue_ct along z)
+template <typename T>
+static cudaError_t enqueue_ct2z(mhd_ctx* ctx) {
+  if (mhd::axis_is_flat(ctx->g, 2)) {
+    cudaError_t e = enqueue_ct<T>(ctx, 2);
+    return e != cudaSuccess ? e : enqueue_ct<T>(ctx, 2);
+  }
+  ProfScope ps(ctx, 5);
+  FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
+  cudaError_t e = Launch<T>::ct2z(ctx->g, in, out, ctx->cfg.h, ctx->ds, ctx->stream);
+  for (int k = 5; k < 8; ++k) ctx->cur[k] ^= 1;
+  return e;
+}
+
 template <typename T>
 static cudaError_t enqueue_step_t(mhd_ctx* ctx, int phase) {
   cudaError_t e;
@@ -117,12 +138,20 @@ static cudaError_t enqueue_step_t(mhd_ctx* ctx, int phase) {
   }
   if (e != cudaSuccess) return e;
   const int* o = kOrder[phase];
+  // the two CT operators of the middle axis meet (forward L ends with CT, reverse L starts
+  // with it): along z they run as one launch (the same bits, one pass over memory less)
+  const bool pair_z = o[2] == 2 && kPairZ;
   for (int k = 0; k < 3; ++k) {
     if ((e = enqueue_fluid<T>(ctx, o[k], false)) != cudaSuccess) return e;
-    if ((e = enqueue_ct<T>(ctx, o[k])) != cudaSuccess) return e;
+    if (k == 2 && pair_z) {
+      if ((e = enqueue_ct2z<T>(ctx)) != cudaSuccess) return e;
+    } else if ((e = enqueue_ct<T>(ctx, o[k])) != cudaSuccess) {
+      return e;
+    }
   }
   for (int k = 2; k >= 0; --k) {
-    if ((e = enqueue_ct<T>(ctx, o[k])) != cudaSuccess) return e;
+    if (!(k == 2 && pair_z))
+      if ((e = enqueue_ct<T>(ctx, o[k])) != cudaSuccess) return e;
     if ((e = enqueue_fluid<T>(ctx, o[k], k == 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -141,23 +170,34 @@ static mhd_status launch_step(mhd_ctx* ctx) {
     return MHD_OK;
   }
   const unsigned sig = cur_sig(ctx);
-  if (!ctx->graph[ph] || ctx->graph_sig[ph] != sig) {
-    if (ctx->graph[ph]) {
-      cudaGraphExecDestroy(ctx->graph[ph]);
-      ctx->graph[ph] = nullptr;
+  mhd_ctx::StepGraph* sg = nullptr;
+  for (auto& c : ctx->graph[ph])
+    if (c.exec && c.sig_in == sig) sg = &c;
+  if (!sg) {
+    sg = &ctx->graph[ph][ctx->graph_next[ph]];
+    ctx->graph_next[ph] ^= 1;
+    if (sg->exec) {
+      cudaGraphExecDestroy(sg->exec);
+      sg->exec = nullptr;
     }
+    const int cur0[8] = {ctx->cur[0], ctx->cur[1], ctx->cur[2], ctx->cur[3],
+                         ctx->cur[4], ctx->cur[5], ctx->cur[6], ctx->cur[7]};
     cudaGraph_t gr = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = enqueue_step(ctx, ph);
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &gr);
+    const unsigned sig_out = cur_sig(ctx);
+    for (int k = 0; k < 8; ++k) ctx->cur[k] = cur0[k];   // applied below, with the launch
     if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(ctx, e, "capture step"); }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "end capture");
-    e = cudaGraphInstantiate(&ctx->graph[ph], gr, 0);
+    e = cudaGraphInstantiate(&sg->exec, gr, 0);
     cudaGraphDestroy(gr);
-    if (e != cudaSuccess) { ctx->graph[ph] = nullptr; return cuda_fail(ctx, e, "instantiate"); }
-    ctx->graph_sig[ph] = sig;   // a step leaves cur[] as it found it
+    if (e != cudaSuccess) { sg->exec = nullptr; return cuda_fail(ctx, e, "instantiate"); }
+    sg->sig_in = sig;
+    sg->sig_out = sig_out;
   }
-  CK(cudaGraphLaunch(ctx->graph[ph], ctx->stream), "graph launch");
+  CK(cudaGraphLaunch(sg->exec, ctx->stream), "graph launch");
+  for (int k = 0; k < 8; ++k) ctx->cur[k] = (int)((sg->sig_out >> k) & 1u);
   ctx->phase = (ph + 1) % 3;
   return MHD_OK;
 }
@@ -221,7 +261,8 @@ void mhd_destroy(mhd_ctx* ctx) {
   for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   for (int p = 0; p < 3; ++p)
-    if (ctx->graph[p]) cudaGraphExecDestroy(ctx->graph[p]);
+    for (auto& c : ctx->graph[p])
+      if (c.exec) cudaGraphExecDestroy(c.exec);
   for (int b = 0; b < 2; ++b)
     for (int k = 0; k < 8; ++k)
       if (ctx->buf[b][k]) cudaFree(ctx->buf[b][k]);
@@ -442,13 +483,18 @@ mhd_status mhd_step(mhd_ctx* ctx, int nsteps, double t_end, int* steps_done, dou
 }
 
 mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt) {
-  if (!ctx || axis < 0 || axis > 2 || (op != 0 && op != 1)) return MHD_ERR_INVALID;
+  if (!ctx || axis < 0 || axis > 2 || op < 0 || op > 2 || (op == 2 && axis != 2))
+    return MHD_ERR_INVALID;
   mhd_status s = sync_scalars(ctx);
   if (s != MHD_OK) return s;
   CK(cudaMemcpyAsync(&ctx->ds->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "dt");
   cudaError_t e;
-  if (ctx->esz == 4) e = op == 0 ? enqueue_fluid<float>(ctx, axis, false) : enqueue_ct<float>(ctx, axis);
-  else e = op == 0 ? enqueue_fluid<double>(ctx, axis, false) : enqueue_ct<double>(ctx, axis);
+  if (ctx->esz == 4)
+    e = op == 0 ? enqueue_fluid<float>(ctx, axis, false)
+                : op == 1 ? enqueue_ct<float>(ctx, axis) : enqueue_ct2z<float>(ctx);
+  else
+    e = op == 0 ? enqueue_fluid<double>(ctx, axis, false)
+                : op == 1 ? enqueue_ct<double>(ctx, axis) : enqueue_ct2z<double>(ctx);
   CK(e, "apply");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   return MHD_OK;

@@ -37,8 +37,12 @@ struct mhd_ctx {
   int step = 0;
   int steps_base = 0;           // ds->steps_done at the last synchronisation point
   int status = 0;               // sticky ST_* bits seen at synchronisation points
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-  unsigned graph_sig[3] = {0, 0, 0};
+  // captured steps: per phase, up to two buffer states (a step whose middle CT_z pair runs
+  // as one launch flips the B buffers once, so the state alternates); sig_in / sig_out: the
+  // buffer assignment (cur[]) before and after the step
+  struct StepGraph { cudaGraphExec_t exec = nullptr; unsigned sig_in = 0, sig_out = 0; };
+  StepGraph graph[3][2];
+  int graph_next[3] = {0, 0, 0};
   long long dev_bytes = 0;
   std::string err;
   // kernel timing mode: steps are launched kernel by kernel with CUDA events around each

@@ -173,6 +173,27 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
 }
 
 template <typename T>
+static cudaError_t ct2z_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
+                             double h, DevScalars* ds, cudaStream_t s) {
+  if (axis_is_flat(g, 2)) return cudaErrorNotSupported;
+  const bool clamp = g.bc[2] == 1;
+  if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
+    constexpr int K = 2, SEG = 32 * K - 16;
+    const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
+    const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
+    if (clamp) ct_seg_z<T, kSegWarps, K, 2, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+    else ct_seg_z<T, kSegWarps, K, 2, false><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+    return cudaGetLastError();
+  }
+  constexpr int K = SegK<T>::K, SEG = 32 * K - 16;
+  const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
+  const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
+  if (clamp) ct_seg_z<T, kSegWarps, K, 2, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+  else ct_seg_z<T, kSegWarps, K, 2, false><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+  return cudaGetLastError();
+}
+
+template <typename T>
 static cudaError_t cmax_impl(const GridDesc& g, const FieldSet<T>& in, double gamma,
                              DevScalars* ds, int pm, cudaStream_t s) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -217,6 +238,10 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
   template <> cudaError_t Launch<T>::ct(const GridDesc& g, const FieldSet<T>& in,           \
       const FieldSet<T>& out, double h, DevScalars* ds, int axis, cudaStream_t s) {         \
     return ct_impl<T>(g, in, out, h, ds, axis, s);                                          \
+  }                                                                                         \
+  template <> cudaError_t Launch<T>::ct2z(const GridDesc& g, const FieldSet<T>& in,         \
+      const FieldSet<T>& out, double h, DevScalars* ds, cudaStream_t s) {                   \
+    return ct2z_impl<T>(g, in, out, h, ds, s);                                              \
   }                                                                                         \
   template <> cudaError_t Launch<T>::cmax(const GridDesc& g, const FieldSet<T>& in,         \
       double gamma, DevScalars* ds, int pm, cudaStream_t s) {                             \

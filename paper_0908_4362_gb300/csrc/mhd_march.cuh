@@ -283,9 +283,18 @@ __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, cons
 // warps march independently as in the per-element staging.
 constexpr int kVecRows = 10;
 
+// 16-byte copies allocate in L1 (.ca, MHD_STAGE_L1 = 1: neighbouring warps' halo rows hit
+// there) or go through L2 only (.cg, 0)
+#ifndef MHD_STAGE_L1
+#define MHD_STAGE_L1 0
+#endif
 __device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+#if MHD_STAGE_L1
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+#else
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+#endif
 }
 
 template <int A, bool LAST, int PM, int S, int NT>

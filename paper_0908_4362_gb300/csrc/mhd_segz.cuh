@@ -7,6 +7,8 @@
 // Per-cell arithmetic and its order are the oracle's (Algorithms 1 and 2).
 #pragma once
 
+#include <type_traits>
+
 #include "mhd_kernels.cuh"
 #include "mhd_march.cuh"
 
@@ -344,11 +346,55 @@ __device__ __forceinline__ void emf_seg2(const float2 (&vf)[K], float2 (&bt)[K],
   for (int i = 0; i < K; ++i) bt[i] = fma2(ndth, sub2(e2[i], e2m[i]), bt[i]);
 }
 
-template <typename T, int K, bool NC>
+// the value of window cell idx (lane idx / K, element idx % K) of a per-lane K array, in
+// every lane
+template <typename V, int K>
+__device__ __forceinline__ V window_cell(const V (&x)[K], int idx) {
+  const int e = idx % K;
+  V v = x[0];
+#pragma unroll
+  for (int i = 1; i < K; ++i) v = (e == i) ? x[i] : v;
+  if constexpr (std::is_same<V, float2>::value) {
+    return V{__shfl_sync(0xffffffffu, v.x, idx / K), __shfl_sync(0xffffffffu, v.y, idx / K)};
+  } else {
+    return __shfl_sync(0xffffffffu, v, idx / K);
+  }
+}
+
+// Between the two passes of an outflow z axis, window cells outside the grid must hold their
+// edge cell's first-pass values (a second single pass would read them clamped from the first
+// pass's output): copy the edge cell's values over, where the edge cell's first-pass value is
+// valid (window cells 4 .. 32K-5).
+template <typename V, int K>
+__device__ __forceinline__ void reclamp_window(V (&x)[K], int zw0, int z0, int nz) {
+  const int lo = -zw0, hi = nz - 1 - zw0;    // window indices of the cells z = 0, nz - 1
+  if (lo >= 4 && lo < 32 * K - 4) {
+    const V v = window_cell<V, K>(x, lo);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (z0 + i < 0) x[i] = v;
+  }
+  if (hi >= 4 && hi < 32 * K - 4) {
+    const V v = window_cell<V, K>(x, hi);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (z0 + i >= nz) x[i] = v;
+  }
+}
+
+// PASSES = 2: the constrained transport along z applied twice with the same dt (the two
+// CT_z operators that meet in the middle of a step whose axis order ends with z, Eq.
+// "eq:L_sequence": forward L_z ends with CT_z, reverse L_z starts with it).  The fluid is
+// frozen, so both passes use the same face velocities; the second pass takes the first
+// pass's advected B_t of the pencil and of its upper rows (the warp's upper-row pipelines
+// advect exactly what the neighbouring pencils' own pipelines advect) and adds its EMF
+// differences to the first pass's B_z.  Every cell runs the operations of two single passes
+// in the same order, so the result is the same bits; the halo doubles (8 cells per side).
+template <typename T, int K, bool NC, int PASSES = 1, bool CLAMPZ = false>
 __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                               const FieldSet<T>& out, double h, DevScalars* ds,
                                               long long wid) {
-  constexpr int H = 4, SEG = 32 * K - 2 * H;
+  constexpr int H = 4 * PASSES, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
   const SegPlace sp = seg_place(g, nz, SEG, wid);
@@ -389,6 +435,9 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
   T eo1[K], en1[K], eo2[K], en2[K];
   constexpr bool PACK = sizeof(T) == 4 && MHD_CT_PACK;
   const T dc = PACK ? dth * T(kEmf2Inv) : dth;   // constraint factor for the EMFs' scale
+  T bA[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) bA[i] = ba[i];
   if constexpr (PACK) {
     // the own-row pipelines of t1 and t2 as one packed pair, the upper-row ones as another
     float2 vo[K], vn[K], bo[K], bh[K], eo[K], en[K];
@@ -401,41 +450,67 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
     }
     const float2 ndth2 = splat2(-(float)dth * kEmf2Inv);
     const float2 nhd2 = splat2(-(float)hd * kEmf2Inv);
-    emf_seg2<K>(vo, bo, ndth2, nhd2, eo);
-    emf_seg2<K>(vn, bh, ndth2, nhd2, en);
+#pragma unroll
+    for (int pass = 0; pass < PASSES; ++pass) {
+      emf_seg2<K>(vo, bo, ndth2, nhd2, eo);
+      emf_seg2<K>(vn, bh, ndth2, nhd2, en);
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        bA[i] = ffma(dc, en[i].x - eo[i].x, bA[i]);   // constraint from t1 = x, then t2 = y
+        bA[i] = ffma(dc, en[i].y - eo[i].y, bA[i]);
+      }
+      if (CLAMPZ && pass + 1 < PASSES) {
+        reclamp_window<float2, K>(bo, s0 - H, z0, nz);
+        reclamp_window<float2, K>(bh, s0 - H, z0, nz);
+        reclamp_window<T, K>(bA, s0 - H, z0, nz);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       b1o[i] = bo[i].x; b2o[i] = bo[i].y;
-      eo1[i] = eo[i].x; eo2[i] = eo[i].y;
-      en1[i] = en[i].x; en2[i] = en[i].y;
     }
   } else {
-    emf_seg<T, K>(vo1, b1o, dth, hd, eo1);
-    emf_seg<T, K>(vn1, b1h, dth, hd, en1);
-    emf_seg<T, K>(vo2, b2o, dth, hd, eo2);
-    emf_seg<T, K>(vn2, b2h, dth, hd, en2);
+#pragma unroll
+    for (int pass = 0; pass < PASSES; ++pass) {
+      emf_seg<T, K>(vo1, b1o, dth, hd, eo1);
+      emf_seg<T, K>(vn1, b1h, dth, hd, en1);
+      emf_seg<T, K>(vo2, b2o, dth, hd, eo2);
+      emf_seg<T, K>(vn2, b2h, dth, hd, en2);
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        bA[i] = ffma(dc, en1[i] - eo1[i], bA[i]);     // constraint from t1 = x, then t2 = y
+        bA[i] = ffma(dc, en2[i] - eo2[i], bA[i]);
+      }
+      if (CLAMPZ && pass + 1 < PASSES) {
+        reclamp_window<T, K>(b1o, s0 - H, z0, nz);
+        reclamp_window<T, K>(b1h, s0 - H, z0, nz);
+        reclamp_window<T, K>(b2o, s0 - H, z0, nz);
+        reclamp_window<T, K>(b2h, s0 - H, z0, nz);
+        reclamp_window<T, K>(bA, s0 - H, z0, nz);
+      }
+    }
   }
   int st = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const int w = lane * K + i, z = z0 + i;
-    T bA = ffma(dc, en1[i] - eo1[i], ba[i]);     // constraint from t1 = x, then t2 = y
-    bA = ffma(dc, en2[i] - eo2[i], bA);
     if (warp_active && w >= H && w < H + SEG && z < nz) {
       const long long co = row + z;
       out.f[5][co] = b1o[i];
       out.f[6][co] = b2o[i];
-      out.f[7][co] = bA;
-      if (!(b1o[i] == b1o[i]) || !(b2o[i] == b2o[i]) || !(bA == bA)) st |= ST_NONFINITE;
+      out.f[7][co] = bA[i];
+      if (!(b1o[i] == b1o[i]) || !(b2o[i] == b2o[i]) || !(bA[i] == bA[i])) st |= ST_NONFINITE;
     }
   }
   if (st) atomicOr(&ds->status, st);
 }
 
-template <typename T, int NW, int K>
+// CLAMPZ: the z axis is outflow (the two-pass form re-clamps its ghost cells between passes)
+template <typename T, int NW, int K, int PASSES = 1, bool CLAMPZ = false>
 __global__ void __launch_bounds__(32 * NW, SegMinBlocks<T>::ct)
 ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
-  ct_seg_z_warp<T, K, true>(g, in, out, h, ds, (long long)blockIdx.x * NW + (threadIdx.x >> 5));
+  ct_seg_z_warp<T, K, true, PASSES, CLAMPZ>(g, in, out, h, ds,
+                                            (long long)blockIdx.x * NW + (threadIdx.x >> 5));
 }
 
 }  // namespace mhd

@@ -369,3 +369,32 @@ def test_invalid_config_rejected(mhd):
         mhd.Solver((0, 4, 4))
     with pytest.raises(mhd.MhdError):
         mhd.Solver((4, 4, 4), cfl=1.5)
+
+
+PAIR_CASES = [("periodic_k3", lambda: I.random_smooth((9, 7, 200), seed=31)),
+              ("outflow_k3", lambda: I.random_smooth((6, 8, 130), seed=32, bc=(1, 1, 1))),
+              ("mixed_k2", lambda: I.random_smooth((10, 9, 40), seed=33, bc=(0, 1, 0))),
+              ("short_z", lambda: I.random_smooth((5, 6, 12), seed=34, bc=(1, 0, 1))),
+              ("blast", lambda: I.blast3d(48))]
+
+
+@pytest.mark.parametrize("case", PAIR_CASES, ids=[c[0] for c in PAIR_CASES])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_ct_z_pair_in_one_launch(mhd, case, prec):
+    """The two CT_z operators that meet in the middle of a step, in one launch (op 2): the
+    same bits as two single CT_z launches, and the oracle's two CT_z within tolerance."""
+    prob = case[1]()
+    p = mhd.FP64 if prec == "fp64" else mhd.FP32
+    ref = oracle.Oracle.from_problem(prob)
+    dt = 0.5 * ref.dt()
+    ref.ct(2, dt)
+    ref.ct(2, dt)
+    got = []
+    for ops in ((1, 1), (2,)):
+        with mhd.Solver.from_problem(prob, prec=p) as s:
+            for op in ops:
+                s.apply(op, 2, dt)
+            got.append(s.read())
+    assert np.array_equal(got[0], got[1]), np.abs(got[0] - got[1]).max()
+    err = rel_l1(got[1], ref.f)
+    assert np.all(err <= (1e-13 if p == mhd.FP64 else 4e-6)), err
