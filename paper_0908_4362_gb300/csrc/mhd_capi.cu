@@ -16,12 +16,15 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/mhd.h"
 #include "mhd_flat.cuh"
 #include "mhd_kernels.cuh"
 #include "mhd_launch.h"
+#include "mhd_tma.cuh"
 
 using mhd::DevScalars;
 using mhd::FieldSet;
@@ -92,8 +95,16 @@ template <typename T>
 static cudaError_t enqueue_fluid(mhd_ctx* ctx, int axis, bool last) {
   ProfScope ps(ctx, axis);
   FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
+  mhd::TmaMaps maps;
+  if (ctx->tma)
+    for (int k = 0; k < 8; ++k) {
+      maps.one[k] = ctx->tmap_one[ctx->cur[k]][k];
+      maps.gx[k] = ctx->tmap_gx[ctx->cur[k]][k];
+      maps.gy[k] = ctx->tmap_gy[ctx->cur[k]][k];
+    }
   cudaError_t e = Launch<T>::fluid(ctx->g, in, out, ctx->cfg.gamma, ctx->cfg.h, ctx->ds, axis,
-                                   last, ctx->cfg.fp64_pressure, ctx->stream);
+                                   last, ctx->cfg.fp64_pressure, ctx->stream,
+                                   ctx->tma ? &maps : nullptr);
   if (!mhd::axis_is_flat(ctx->g, axis))   // along a flat axis the sweep is the identity
     for (int k = 0; k < 5; ++k) ctx->cur[k] ^= 1;
   return e;
@@ -203,6 +214,7 @@ static mhd_status launch_step(mhd_ctx* ctx) {
 }
 
 static mhd_status status_from(int st) {
+  if (st & mhd::ST_TIMEOUT) return MHD_ERR_TIMEOUT;
   return st ? MHD_ERR_UNPHYSICAL : MHD_OK;
 }
 
@@ -237,6 +249,45 @@ static mhd_status compute_cmax(mhd_ctx* ctx) {
   }
   CK(e, "cmax");
   return MHD_OK;
+}
+
+// Tensor maps of the state buffers for the TMA-staged sweeps: each buffer as a 3D FP32 tensor
+// (z, y, x) with boxes of 128 x 1 x 1 elements.  The encoding entry point comes from the
+// driver through the runtime (no link-time dependency on the driver library).  Any failure
+// leaves ctx->tma false (the sweeps then use the cp.async staging).
+static void make_tensor_maps(mhd_ctx* ctx) {
+  ctx->tma = false;
+  if (!MHD_TMA_MARCH || ctx->esz != 4 || ctx->g.n[2] % 128 != 0) return;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)ctx->g.n[2], (cuuint64_t)ctx->g.n[1],
+                              (cuuint64_t)ctx->g.n[0]};
+  const cuuint64_t strides[2] = {(cuuint64_t)ctx->g.n[2] * 4,
+                                 (cuuint64_t)ctx->g.n[2] * ctx->g.n[1] * 4};
+  const cuuint32_t G = mhd::kTmaG;
+  const cuuint32_t box_one[3] = {128, 1, 1}, box_gx[3] = {128, 1, G}, box_gy[3] = {128, G, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  auto enc = [&](CUtensorMap* m, void* base, const cuuint32_t* box) {
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 8; ++k)
+      if (!enc(&ctx->tmap_one[b][k], ctx->buf[b][k], box_one) ||
+          !enc(&ctx->tmap_gx[b][k], ctx->buf[b][k], box_gx) ||
+          !enc(&ctx->tmap_gy[b][k], ctx->buf[b][k], box_gy))
+        return;
+  ctx->tma = true;
 }
 
 extern "C" {
@@ -330,6 +381,7 @@ mhd_status mhd_create(const mhd_config* cfg, mhd_ctx** out) {
       if (e != cudaSuccess) { cuda_fail(ctx, e, "state allocation"); return fail(MHD_ERR_OOM); }
       ctx->dev_bytes += (long long)fb;
     }
+  make_tensor_maps(ctx);
   e = cudaMalloc(&ctx->staging, (size_t)ctx->N * sizeof(double));
   if (e != cudaSuccess) { cuda_fail(ctx, e, "staging allocation"); return fail(MHD_ERR_OOM); }
   ctx->dev_bytes += (long long)ctx->N * 8;

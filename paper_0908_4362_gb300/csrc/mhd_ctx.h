@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/mhd.h"
@@ -43,6 +44,11 @@ struct mhd_ctx {
   struct StepGraph { cudaGraphExec_t exec = nullptr; unsigned sig_in = 0, sig_out = 0; };
   StepGraph graph[3][2];
   int graph_next[3] = {0, 0, 0};
+  // tensor maps of the 16 state buffers for the TMA-staged x/y fluid sweeps (FP32 grids
+  // with nz a multiple of 128; tma false otherwise), per buffer b and field k: boxes of 128 z
+  // positions of one row (one), of kTmaG rows along x (gx) and along y (gy)
+  bool tma = false;
+  CUtensorMap tmap_one[2][8], tmap_gx[2][8], tmap_gy[2][8];
   long long dev_bytes = 0;
   std::string err;
   // kernel timing mode: steps are launched kernel by kernel with CUDA events around each

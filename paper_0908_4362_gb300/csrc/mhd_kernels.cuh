@@ -19,7 +19,7 @@
 
 namespace mhd {
 
-enum : int { ST_UNPHYSICAL = 1, ST_NONFINITE = 2, ST_BAD_DT = 4 };
+enum : int { ST_UNPHYSICAL = 1, ST_NONFINITE = 2, ST_BAD_DT = 4, ST_TIMEOUT = 8 };
 
 struct GridDesc {
   int n[3];

@@ -14,10 +14,12 @@ template <typename T>
 struct Launch {
   // one-time kernel attribute setup (dynamic shared memory opt-in); not capturable
   static cudaError_t setup();
-  // fluid_axis(dt) with dt read from ds; last: also accumulate c_max of the result
+  // fluid_axis(dt) with dt read from ds; last: also accumulate c_max of the result.
+  // tmaps: NULL, or the tensor maps (TmaMaps, host memory) of the 8 input buffers, for the
+  // TMA-staged x/y sweeps (FP32, nz a multiple of 128)
   static cudaError_t fluid(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                            double gamma, double h, DevScalars* ds, int axis, bool last,
-                           int pm, cudaStream_t s);
+                           int pm, cudaStream_t s, const void* tmaps = nullptr);
   // CT along axis for both transverse components (t1 then t2)
   static cudaError_t ct(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                         double h, DevScalars* ds, int axis, cudaStream_t s);

@@ -6,6 +6,7 @@
 #include "mhd_launch.h"
 #include "mhd_march.cuh"
 #include "mhd_segz.cuh"
+#include "mhd_tma.cuh"
 
 namespace mhd {
 
@@ -27,9 +28,12 @@ static cudaError_t set_march_attr() {
       fluid_march_xy<T, A, LAST, PM, MarchCfg<T>::S, MarchCfg<T>::NT>,
       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
   if constexpr (sizeof(T) == 4) {
-    const cudaError_t e2 = cudaFuncSetAttribute(
+    cudaError_t e2 = cudaFuncSetAttribute(
         fluid_march_xy_vec<A, LAST, PM, MarchCfg<T>::S, MarchCfg<T>::NT>,
         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
+    if (e2 != cudaSuccess) e = e2;
+    e2 = cudaFuncSetAttribute(fluid_march_xy_tma<A, LAST, PM, MarchCfg<T>::S>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_march_smem());
     if (e2 != cudaSuccess) e = e2;
   }
   return e;
@@ -63,9 +67,11 @@ static cudaError_t setup_p() {
   return e;
 }
 
+
 template <typename T, bool LAST, int PM>
 static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
-                           T gamma, double h, DevScalars* ds, int axis, cudaStream_t s) {
+                           T gamma, double h, DevScalars* ds, int axis, cudaStream_t s,
+                           const void* tmaps) {
   constexpr int S = MarchCfg<T>::S, NT = MarchCfg<T>::NT;
   if (axis == 0 || axis == 1) {
     const int o = axis == 0 ? 1 : 0;
@@ -73,6 +79,22 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
     const dim3 grid((unsigned)((np + NT - 1) / NT), (unsigned)((g.n[axis] + S - 1) / S));
     const size_t sm = march_tile_smem<T>();
     if constexpr (sizeof(T) == 4) {
+      if (MHD_TMA_MARCH && tmaps && g.n[2] % 128 == 0) {
+        const TmaMaps* m = static_cast<const TmaMaps*>(tmaps);
+        const int A = axis, T1 = (A + 1) % 3, T2 = (A + 2) % 3;
+        TmaRows rows;
+        const int f[9] = {0, 1 + A, 1 + T1, 1 + T2, 4, 5 + A, 5 + T1, 5 + T2, 5 + o};
+        for (int r = 0; r < 9; ++r) {
+          rows.g[r] = A == 0 ? m->gx[f[r]] : m->gy[f[r]];
+          rows.one[r] = m->one[f[r]];
+        }
+        const size_t tsm = tma_march_smem();
+        if (axis == 0)
+          fluid_march_xy_tma<0, LAST, PM, S><<<grid, 128, tsm, s>>>(g, in, out, gamma, h, ds, rows);
+        else
+          fluid_march_xy_tma<1, LAST, PM, S><<<grid, 128, tsm, s>>>(g, in, out, gamma, h, ds, rows);
+        return;
+      }
       if (march_vec<T>(g)) {
         if (axis == 0) fluid_march_xy_vec<0, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
         else fluid_march_xy_vec<1, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
@@ -103,24 +125,24 @@ static cudaError_t cmax_impl(const GridDesc& g, const FieldSet<T>& in, double ga
 template <typename T>
 static cudaError_t fluid_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                               double gamma, double h, DevScalars* ds, int axis, bool last,
-                              int pm, cudaStream_t s) {
+                              int pm, cudaStream_t s, const void* tmaps) {
   if (axis_is_flat(g, axis))   // identity (mhd_flat.cuh); the caller does not swap buffers
     return last ? cmax_impl<T>(g, in, gamma, ds, pm, s) : cudaSuccess;
   const T gm = (T)gamma;
   if constexpr (sizeof(T) == 4) {
     if (pm == PM_FP64) {
-      if (last) fluid_dispatch<T, true, PM_FP64>(g, in, out, gm, h, ds, axis, s);
-      else fluid_dispatch<T, false, PM_FP64>(g, in, out, gm, h, ds, axis, s);
+      if (last) fluid_dispatch<T, true, PM_FP64>(g, in, out, gm, h, ds, axis, s, tmaps);
+      else fluid_dispatch<T, false, PM_FP64>(g, in, out, gm, h, ds, axis, s, tmaps);
       return cudaGetLastError();
     }
     if (pm == PM_COMP) {
-      if (last) fluid_dispatch<T, true, PM_COMP>(g, in, out, gm, h, ds, axis, s);
-      else fluid_dispatch<T, false, PM_COMP>(g, in, out, gm, h, ds, axis, s);
+      if (last) fluid_dispatch<T, true, PM_COMP>(g, in, out, gm, h, ds, axis, s, tmaps);
+      else fluid_dispatch<T, false, PM_COMP>(g, in, out, gm, h, ds, axis, s, tmaps);
       return cudaGetLastError();
     }
   }
-  if (last) fluid_dispatch<T, true, PM_FP32>(g, in, out, gm, h, ds, axis, s);
-  else fluid_dispatch<T, false, PM_FP32>(g, in, out, gm, h, ds, axis, s);
+  if (last) fluid_dispatch<T, true, PM_FP32>(g, in, out, gm, h, ds, axis, s, tmaps);
+  else fluid_dispatch<T, false, PM_FP32>(g, in, out, gm, h, ds, axis, s, tmaps);
   return cudaGetLastError();
 }
 
@@ -232,8 +254,8 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
   }                                                                                         \
   template <> cudaError_t Launch<T>::fluid(const GridDesc& g, const FieldSet<T>& in,        \
       const FieldSet<T>& out, double gamma, double h, DevScalars* ds, int axis, bool last,  \
-      int pm, cudaStream_t s) {                                                           \
-    return fluid_impl<T>(g, in, out, gamma, h, ds, axis, last, pm, s);                     \
+      int pm, cudaStream_t s, const void* tmaps) {                                          \
+    return fluid_impl<T>(g, in, out, gamma, h, ds, axis, last, pm, s, tmaps);              \
   }                                                                                         \
   template <> cudaError_t Launch<T>::ct(const GridDesc& g, const FieldSet<T>& in,           \
       const FieldSet<T>& out, double h, DevScalars* ds, int axis, cudaStream_t s) {         \

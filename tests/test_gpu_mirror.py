@@ -12,7 +12,8 @@ in FP64, so both take the upwind rule of Eq. "eq:first_flux" there (the symmetri
 parity cases).  A generic state has no exact ties, so the rule is not exercised here.
 
 Shapes: x/y constrained transport with shared EMF rows (nz >= 48) and per pencil, z
-segments of 2 and 3 cells per lane, a ragged tail of the marching tiles along x."""
+segments of 2 and 3 cells per lane, a ragged tail of the marching tiles along x, and a z
+extent of 128 (TMA-staged x/y fluid sweeps)."""
 import numpy as np
 import pytest
 
@@ -30,7 +31,7 @@ def mhd():
     return m
 
 
-SHAPES = [(24, 20, 56), (210, 6, 22), (12, 14, 40)]
+SHAPES = [(24, 20, 56), (210, 6, 22), (12, 14, 40), (20, 6, 128)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=["x".join(map(str, s)) for s in SHAPES])

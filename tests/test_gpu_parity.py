@@ -56,6 +56,10 @@ OP_CASES = [
     # across the other transverse axis
     ("rows_per_block", lambda: I.random_smooth((9, 37, 36), seed=18)),
     ("block_wraps_z", lambda: I.random_smooth((6, 5, 132), seed=19, bc=(1, 1, 0))),
+    # z extents that are multiples of 128 (the TMA-staged x/y fluid sweeps), periodic and
+    # outflow along the sweeps, the tile along x shorter and longer than one march tile
+    ("tma_periodic", lambda: I.random_smooth((37, 5, 128), seed=24)),
+    ("tma_outflow", lambda: I.random_smooth((200, 3, 256), seed=25, bc=(1, 1, 1))),
 ]
 
 
@@ -90,6 +94,7 @@ STEP_CASES = [
     ("batched_instance", lambda: I.batched_instance(3)),
     ("zvec_outflow", lambda: I.random_smooth((13, 11, 72), seed=6, bc=(0, 1, 1))),
     ("long_mixed", lambda: I.random_smooth((131, 9, 68), seed=17, bc=(1, 0, 1))),
+    ("tma_mixed", lambda: I.random_smooth((21, 13, 128), seed=26, bc=(0, 1, 0))),
     ("dai_woodward_256", lambda: I.dai_woodward(256)),
     ("blast2d_64", lambda: I.blast2d(64)),
     ("rotor1_64", lambda: I.rotor(64, 1)),
