@@ -92,10 +92,10 @@ mhd_status mhd_upload(mhd_ctx* ctx, const void* const f[8], int dtype, int on_de
 mhd_status mhd_step(mhd_ctx* ctx, int nsteps, double t_end, int* steps_done, double* t_now);
 
 /* Apply one sweep operator with a given dt, for testing: op 0 = fluid_axis (Algorithm 1),
- * op 1 = CT along axis for both transverse components (Algorithm 2), op 2 = CT along z
- * twice (axis must be 2; the pair of CT_z operators that meet in the middle of a step whose
- * axis order ends with z, Eq. "eq:L_sequence", in one launch; the same result as op 1
- * applied twice).  Returns after the operator completed. */
+ * op 1 = CT along axis for both transverse components (Algorithm 2), op 2 = CT along axis
+ * twice (the pair of CT operators that meet in the middle of a step whose axis order ends
+ * with that axis, Eq. "eq:L_sequence": one launch where the library has a two-pass kernel,
+ * else two; the same result as op 1 applied twice).  Returns after the operator completed. */
 mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt);
 
 /* c_max of the current state (Eq. "equat_CFL").  Blocking. */

@@ -5,12 +5,12 @@
 // left by the previous step into dt (clipped to t_end) and advances t; then the forward
 // sweep applies, for the axis order (a, b, c) of the current phase, fluid_a, CT_a,
 // fluid_b, CT_b, fluid_c, CT_c, and the reverse sweep CT_c, fluid_c, CT_b, fluid_b, CT_a,
-// fluid_a (reverse L: magnetic updates first, Sect. 4.3); where c is z, the two CT_z in the
-// middle run as one launch.  The last fluid sweep also reduces the next c_max.  Each sweep is
+// fluid_a (reverse L: magnetic updates first, Sect. 4.3); the two CT_c in the middle run as
+// one launch where a two-pass kernel exists (z; x and y in the shared-row form, periodic).  The last fluid sweep also reduces the next c_max.  Each sweep is
 // out of place; the context tracks which of the two buffers holds each field.  A step's
 // launch sequence depends on the phase and on the buffer state it starts from, which
-// alternates between two states (the middle CT_z pair flips the B buffers once), so each
-// phase keeps up to two captured CUDA graphs.
+// alternates between two states (a middle CT pair in one launch flips the B buffers once), so
+// each phase keeps up to two captured CUDA graphs.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -120,24 +120,32 @@ static cudaError_t enqueue_ct(mhd_ctx* ctx, int axis) {
   return e;
 }
 
-// the middle CT_z pair of a step runs as one launch (MHD_PAIR_Z = 1) or as two (0)
-#ifndef MHD_PAIR_Z
-#define MHD_PAIR_Z 1
+// the middle CT pair of a step runs as one launch where a two-pass kernel exists
+// (MHD_PAIR = 1) or always as two (0)
+#ifndef MHD_PAIR
+#define MHD_PAIR 1
 #endif
-static constexpr bool kPairZ = MHD_PAIR_Z != 0;
+static constexpr bool kPair = MHD_PAIR != 0;
 
-// CT along z twice (one launch, the same bits as two enqueue_ct along z)
+// CT along axis twice: one launch where a two-pass kernel exists (the same bits as two
+// enqueue_ct), else two launches
 template <typename T>
-static cudaError_t enqueue_ct2z(mhd_ctx* ctx) {
-  if (mhd::axis_is_flat(ctx->g, 2)) {
-    cudaError_t e = enqueue_ct<T>(ctx, 2);
-    return e != cudaSuccess ? e : enqueue_ct<T>(ctx, 2);
+static cudaError_t enqueue_ct2(mhd_ctx* ctx, int axis) {
+  if (kPair && !mhd::axis_is_flat(ctx->g, axis)) {
+    FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
+    cudaError_t e;
+    {
+      ProfScope ps(ctx, 3 + axis);
+      e = Launch<T>::ct2(ctx->g, in, out, ctx->cfg.h, ctx->ds, axis, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+      for (int k = 5; k < 8; ++k) ctx->cur[k] ^= 1;
+      return e;
+    }
+    if (e != cudaErrorNotSupported) return e;   // (no kernel launched: nothing to clear)
   }
-  ProfScope ps(ctx, 5);
-  FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
-  cudaError_t e = Launch<T>::ct2z(ctx->g, in, out, ctx->cfg.h, ctx->ds, ctx->stream);
-  for (int k = 5; k < 8; ++k) ctx->cur[k] ^= 1;
-  return e;
+  cudaError_t e = enqueue_ct<T>(ctx, axis);
+  return e != cudaSuccess ? e : enqueue_ct<T>(ctx, axis);
 }
 
 template <typename T>
@@ -150,18 +158,18 @@ static cudaError_t enqueue_step_t(mhd_ctx* ctx, int phase) {
   if (e != cudaSuccess) return e;
   const int* o = kOrder[phase];
   // the two CT operators of the middle axis meet (forward L ends with CT, reverse L starts
-  // with it): along z they run as one launch (the same bits, one pass over memory less)
-  const bool pair_z = o[2] == 2 && kPairZ;
+  // with it): they run as one launch where a two-pass kernel exists (the same bits, one pass
+  // over memory less)
   for (int k = 0; k < 3; ++k) {
     if ((e = enqueue_fluid<T>(ctx, o[k], false)) != cudaSuccess) return e;
-    if (k == 2 && pair_z) {
-      if ((e = enqueue_ct2z<T>(ctx)) != cudaSuccess) return e;
+    if (k == 2) {
+      if ((e = enqueue_ct2<T>(ctx, o[k])) != cudaSuccess) return e;
     } else if ((e = enqueue_ct<T>(ctx, o[k])) != cudaSuccess) {
       return e;
     }
   }
   for (int k = 2; k >= 0; --k) {
-    if (!(k == 2 && pair_z))
+    if (k != 2)
       if ((e = enqueue_ct<T>(ctx, o[k])) != cudaSuccess) return e;
     if ((e = enqueue_fluid<T>(ctx, o[k], k == 0)) != cudaSuccess) return e;
   }
@@ -535,18 +543,17 @@ mhd_status mhd_step(mhd_ctx* ctx, int nsteps, double t_end, int* steps_done, dou
 }
 
 mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt) {
-  if (!ctx || axis < 0 || axis > 2 || op < 0 || op > 2 || (op == 2 && axis != 2))
-    return MHD_ERR_INVALID;
+  if (!ctx || axis < 0 || axis > 2 || op < 0 || op > 2) return MHD_ERR_INVALID;
   mhd_status s = sync_scalars(ctx);
   if (s != MHD_OK) return s;
   CK(cudaMemcpyAsync(&ctx->ds->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "dt");
   cudaError_t e;
   if (ctx->esz == 4)
     e = op == 0 ? enqueue_fluid<float>(ctx, axis, false)
-                : op == 1 ? enqueue_ct<float>(ctx, axis) : enqueue_ct2z<float>(ctx);
+                : op == 1 ? enqueue_ct<float>(ctx, axis) : enqueue_ct2<float>(ctx, axis);
   else
     e = op == 0 ? enqueue_fluid<double>(ctx, axis, false)
-                : op == 1 ? enqueue_ct<double>(ctx, axis) : enqueue_ct2z<double>(ctx);
+                : op == 1 ? enqueue_ct<double>(ctx, axis) : enqueue_ct2<double>(ctx, axis);
   CK(e, "apply");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   return MHD_OK;

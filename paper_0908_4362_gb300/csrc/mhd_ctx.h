@@ -38,8 +38,8 @@ struct mhd_ctx {
   int step = 0;
   int steps_base = 0;           // ds->steps_done at the last synchronisation point
   int status = 0;               // sticky ST_* bits seen at synchronisation points
-  // captured steps: per phase, up to two buffer states (a step whose middle CT_z pair runs
-  // as one launch flips the B buffers once, so the state alternates); sig_in / sig_out: the
+  // captured steps: per phase, up to two buffer states (a step whose middle CT pair runs as
+  // one launch flips the B buffers once, so the state alternates); sig_in / sig_out: the
   // buffer assignment (cur[]) before and after the step
   struct StepGraph { cudaGraphExec_t exec = nullptr; unsigned sig_in = 0, sig_out = 0; };
   StepGraph graph[3][2];

@@ -23,10 +23,11 @@ struct Launch {
   // CT along axis for both transverse components (t1 then t2)
   static cudaError_t ct(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                         double h, DevScalars* ds, int axis, cudaStream_t s);
-  // CT along z applied twice in one launch (the middle pair of a step whose axis order ends
-  // with z); cudaErrorNotSupported for a flat z axis
-  static cudaError_t ct2z(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
-                          double h, DevScalars* ds, cudaStream_t s);
+  // CT along axis applied twice in one launch (the middle pair of a step whose axis order
+  // ends with that axis); cudaErrorNotSupported where there is no such kernel (a flat axis;
+  // x/y outside the shared-row form or with an outflow sweep axis)
+  static cudaError_t ct2(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
+                         double h, DevScalars* ds, int axis, cudaStream_t s);
   static cudaError_t cmax(const GridDesc& g, const FieldSet<T>& in, double gamma,
                           DevScalars* ds, int pm, cudaStream_t s);
   static cudaError_t dt(DevScalars* ds, double cfl_h, cudaStream_t s);

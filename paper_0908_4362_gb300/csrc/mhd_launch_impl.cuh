@@ -50,9 +50,13 @@ static cudaError_t set_ct_march_attr() {
 constexpr int kRowsR = MHD_ROWS_R;
 template <typename T, int A>
 static cudaError_t set_ct_rows_attr() {
-  return cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, kRowsR>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)ct_rows_smem<T>(kRowsR));
+  cudaError_t e = cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, kRowsR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ct_rows_smem<T>(kRowsR));
+  const cudaError_t e2 = cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, kRowsR, 2>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)ct_rows_smem<T>(kRowsR, 2));
+  return e != cudaSuccess ? e : e2;
 }
 
 template <typename T, int PM>
@@ -195,9 +199,20 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
 }
 
 template <typename T>
-static cudaError_t ct2z_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
-                             double h, DevScalars* ds, cudaStream_t s) {
-  if (axis_is_flat(g, 2)) return cudaErrorNotSupported;
+static cudaError_t ct2_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
+                            double h, DevScalars* ds, int axis, cudaStream_t s) {
+  if (axis_is_flat(g, axis)) return cudaErrorNotSupported;
+  if (axis < 2) {
+    if (!ct_use_rows(g, axis) || g.bc[axis] != 0) return cudaErrorNotSupported;
+    constexpr int S = MarchCfg<T>::S, R = kRowsR;
+    const int o = axis == 0 ? 1 : 0;
+    const long long nb = (long long)((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1));
+    const dim3 grid((unsigned)nb, (unsigned)((g.n[axis] + S - 1) / S));
+    const size_t sm = ct_rows_smem<T>(R, 2);
+    if (axis == 0) ct_rows_xy<T, 0, S, R, 2><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
+    else ct_rows_xy<T, 1, S, R, 2><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
+    return cudaGetLastError();
+  }
   const bool clamp = g.bc[2] == 1;
   if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
     constexpr int K = 2, SEG = 32 * K - 16;
@@ -261,9 +276,9 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
       const FieldSet<T>& out, double h, DevScalars* ds, int axis, cudaStream_t s) {         \
     return ct_impl<T>(g, in, out, h, ds, axis, s);                                          \
   }                                                                                         \
-  template <> cudaError_t Launch<T>::ct2z(const GridDesc& g, const FieldSet<T>& in,         \
-      const FieldSet<T>& out, double h, DevScalars* ds, cudaStream_t s) {                   \
-    return ct2z_impl<T>(g, in, out, h, ds, s);                                              \
+  template <> cudaError_t Launch<T>::ct2(const GridDesc& g, const FieldSet<T>& in,          \
+      const FieldSet<T>& out, double h, DevScalars* ds, int axis, cudaStream_t s) {         \
+    return ct2_impl<T>(g, in, out, h, ds, axis, s);                                         \
   }                                                                                         \
   template <> cudaError_t Launch<T>::cmax(const GridDesc& g, const FieldSet<T>& in,         \
       double gamma, DevScalars* ds, int pm, cudaStream_t s) {                             \

@@ -763,11 +763,19 @@ __host__ __device__ inline bool ct_use_rows(const GridDesc& g, int axis) {
   return axis < 2 && g.n[2] >= kRowsMinNz && g.n[axis == 0 ? 1 : 0] >= kRowsMinRows;
 }
 
-template <typename T, int A, int S, int R>
+// PASSES = 2: the CT along A applied twice with the same dt in one march (the pair of CT
+// operators in the middle of a step whose axis order ends with A, Eq. "eq:L_sequence"), for a
+// periodic axis A.  A second pair of pipelines runs 4 cells behind the first, fed with the
+// first pass's advected B_t and the same face velocities (the fluid is frozen); its EMFs are
+// exchanged with the first pass's at the same barriers, and its constraint adds to the first
+// pass's B_A.  Each cell gets the operations of two single passes in the same order (the same
+// bits); the tile's halo along A doubles to 8 cells.
+template <typename T, int A, int S, int R, int PASSES = 1>
 __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSet<T>& in,
                                                 const FieldSet<T>& out, double h, DevScalars* ds,
                                                 unsigned bx, unsigned by,
                                                 unsigned char* smem_raw) {
+  static_assert(PASSES == 1 || PASSES == 2, "one or two passes");
   static_assert(A == 0 || A == 1, "x or y sweep");
   constexpr int O = (A == 0) ? 1 : 0;
   constexpr int T1 = axis_t1(A), T2 = axis_t2(A);
@@ -798,39 +806,55 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
   const T* __restrict__ pba = in.f[5 + A];
   const long long sA = g.s[A];
   constexpr bool PACK = MHD_CT_PACK && sizeof(T) == 4;
-  EmfPipe<T> p1, p2;
-  EmfPipe2 pp2;
+  EmfPipe<T> p1, p2, q1, q2;                 // q: the second pass (PASSES = 2)
+  EmfPipe2 pp2, qq2;
   p1.init();
   p2.init();
   pp2.init();
+  q1.init();
+  q2.init();
+  qq2.init();
   const float2 ndth2 = splat2(-(float)dth * kEmf2Inv), nhd2 = splat2(-(float)hd * kEmf2Inv);
   const T dc = PACK ? dth * T(kEmf2Inv) : dth;   // constraint factor for the EMFs' scale
   T ba1 = T(0), ba2 = T(0), ba3 = T(0), ba4 = T(0);
-  const int js = a0 - 4;
-  const int kend = min(S, nA - a0) + 8;
+  // the second pass: face velocities of the last 4 cells, first-pass B_A of the last 4
+  T wv1[4] = {T(0), T(0), T(0), T(0)}, wv2[4] = {T(0), T(0), T(0), T(0)};
+  T wb1 = T(0), wb2 = T(0), wb3 = T(0), wb4 = T(0);
+  constexpr int H = 4 * PASSES;              // halo along A
+  const int js = a0 - H;
+  const int kend = min(S, nA - a0) + 2 * H;
   T* ring = reinterpret_cast<T*>(smem_raw);
-  T* xbuf = ring + (size_t)kMarchRing * 9 * NT;   // [2][NT] EMF of the O pipeline
+  T* xbuf = ring + (size_t)kMarchRing * 9 * NT;   // [2][PASSES][NT] EMF of the O pipelines
   int st = 0;
-  // one cell of the march: face velocities, both EMF pipelines, the EMF exchange and the
+  // the pipelines of one pass for one cell: face velocities vf1, vf2 and B_t in; the
+  // advected B_t (4 cells behind) and the EMFs at its lower A face out
+  auto pipes = [&](EmfPipe<T>& a1, EmfPipe<T>& a2, EmfPipe2& aa, T vf1, T vf2, T b1in,
+                   T b2in, T& bt1, T& bt2, T& e1, T& e2) {
+    if constexpr (PACK) {
+      float2 e12;
+      const float2 bt = aa.push(make_float2((float)vf1, (float)vf2),
+                                make_float2((float)b1in, (float)b2in), ndth2, nhd2, &e12);
+      bt1 = bt.x; bt2 = bt.y; e1 = e12.x; e2 = e12.y;
+    } else {
+      // the halo row only feeds the O pipeline's EMF to the row below
+      if (!halo_row || !Z1) bt1 = a1.push(vf1, b1in, dth, hd, &e1);
+      if (!halo_row || Z1) bt2 = a2.push(vf2, b2in, dth, hd, &e2);
+    }
+  };
+  // one cell of the march: face velocities, the EMF pipelines, the EMF exchange and the
   // constraint on B_A; r = rho (own, lo1, lo2), m = m_A (same), b1, b2, ba the face fields
   auto cell = [&](int k, T r0, T r1, T r2, T m0, T m1, T m2, T b1in, T b2in, T bain) {
     const int j = js + k;
     const T vf1 = Num<T>::div(m0 + m1, r0 + r1);     // face velocities below the pencil
     const T vf2 = Num<T>::div(m0 + m2, r0 + r2);
     T bt1 = T(0), bt2 = T(0), e1 = T(0), e2 = T(0);
-    if constexpr (PACK) {
-      float2 e12;
-      const float2 bt = pp2.push(make_float2((float)vf1, (float)vf2),
-                                 make_float2((float)b1in, (float)b2in), ndth2, nhd2, &e12);
-      bt1 = bt.x; bt2 = bt.y; e1 = e12.x; e2 = e12.y;
-    } else {
-      // the halo row only feeds the O pipeline's EMF to the row below
-      if (!halo_row || !Z1) bt1 = p1.push(vf1, b1in, dth, hd, &e1);
-      if (!halo_row || Z1) bt2 = p2.push(vf2, b2in, dth, hd, &e2);
-    }
-    const T eo = Z1 ? e2 : e1;                       // EMF of the O pipeline
-    T* xb = xbuf + (k & 1) * NT;
-    xb[threadIdx.x] = eo;
+    pipes(p1, p2, pp2, vf1, vf2, b1in, b2in, bt1, bt2, e1, e2);
+    // second pass, 4 cells behind: first-pass B_t of cell j-4 with its face velocities
+    T ct1 = T(0), ct2 = T(0), f1 = T(0), f2 = T(0);
+    if constexpr (PASSES == 2) pipes(q1, q2, qq2, wv1[3], wv2[3], bt1, bt2, ct1, ct2, f1, f2);
+    T* xb = xbuf + (k & 1) * PASSES * NT;
+    xb[threadIdx.x] = Z1 ? e2 : e1;                  // EMF of the O pipeline
+    if constexpr (PASSES == 2) xb[NT + threadIdx.x] = Z1 ? f2 : f1;
 #if MHD_CT_PAIR_BARRIERS
     // warp w hands its value to warp w-1 (barrier w) and takes warp w+1's (barrier w+1):
     // each named barrier joins just the two warps of one row pair (64 threads)
@@ -839,13 +863,30 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
 #else
     __syncthreads();
 #endif
-    const T eo_up = xb[halo_row ? threadIdx.x : threadIdx.x + 32];
+    const int up = halo_row ? threadIdx.x : threadIdx.x + 32;
+    const T eo_up = xb[up];
     const T ez_up = __shfl_down_sync(0xffffffffu, Z1 ? e1 : e2, 1);
     const T en1 = Z1 ? ez_up : eo_up, en2 = Z1 ? eo_up : ez_up;
     T b = ffma(dc, en1 - e1, ba4);           // constraint from t1, then t2
     b = ffma(dc, en2 - e2, b);
     ba4 = ba3; ba3 = ba2; ba2 = ba1; ba1 = bain;
-    if (k >= 8 && out_ok) {
+    if constexpr (PASSES == 2) {
+      const T fo_up = xb[NT + up];
+      const T fz_up = __shfl_down_sync(0xffffffffu, Z1 ? f1 : f2, 1);
+      const T fn1 = Z1 ? fz_up : fo_up, fn2 = Z1 ? fo_up : fz_up;
+      T b2 = ffma(dc, fn1 - f1, wb4);        // the second pass's constraint on cell j-8
+      b2 = ffma(dc, fn2 - f2, b2);
+      wb4 = wb3; wb3 = wb2; wb2 = wb1; wb1 = b;
+      wv1[3] = wv1[2]; wv1[2] = wv1[1]; wv1[1] = wv1[0]; wv1[0] = vf1;
+      wv2[3] = wv2[2]; wv2[2] = wv2[1]; wv2[1] = wv2[0]; wv2[0] = vf2;
+      if (k >= 2 * H && out_ok) {
+        const long long co = base + (long long)(j - 8) * sA;
+        out.f[5 + T1][co] = ct1;
+        out.f[5 + T2][co] = ct2;
+        out.f[5 + A][co] = b2;
+        if (!(ct1 == ct1) || !(ct2 == ct2) || !(b2 == b2)) st |= ST_NONFINITE;
+      }
+    } else if (k >= 8 && out_ok) {
       const long long co = base + (long long)(j - 4) * sA;
       out.f[5 + T1][co] = bt1;
       out.f[5 + T2][co] = bt2;
@@ -940,15 +981,16 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
 }
 
 template <typename T>
-static size_t ct_rows_smem(int R) {
-  return sizeof(T) * ((size_t)kMarchRing * 9 * 32 * R + 2 * 32 * R);
+static size_t ct_rows_smem(int R, int passes = 1) {
+  return sizeof(T) * ((size_t)kMarchRing * 9 * 32 * R + 2 * (size_t)passes * 32 * R);
 }
 
-template <typename T, int A, int S, int R>
-__global__ void __launch_bounds__(32 * R)
+// the two-pass form asks for 2 resident blocks (at most 128 registers a thread)
+template <typename T, int A, int S, int R, int PASSES = 1>
+__global__ void __launch_bounds__(32 * R, PASSES == 2 ? 2 : 0)
 ct_rows_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ct_rows_xy_tile<T, A, S, R>(g, in, out, h, ds, blockIdx.x, blockIdx.y, smem_raw);
+  ct_rows_xy_tile<T, A, S, R, PASSES>(g, in, out, h, ds, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 }  // namespace mhd

@@ -383,22 +383,42 @@ PAIR_CASES = [("periodic_k3", lambda: I.random_smooth((9, 7, 200), seed=31)),
               ("blast", lambda: I.blast3d(48))]
 
 
+# x/y cases: the shared-row CT form (nz >= 48, 4+ rows across) with a periodic sweep axis
+# runs the pair in one launch; outflow along the sweep falls back to two launches
+PAIR_CASES_XY = [("rows_periodic", lambda: I.random_smooth((230, 9, 60), seed=35)),
+                 ("rows_mixed", lambda: I.random_smooth((40, 30, 52), seed=36, bc=(0, 0, 1))),
+                 ("rows_outflow_t", lambda: I.random_smooth((50, 7, 96), seed=37, bc=(0, 1, 1))),
+                 ("outflow_sweep", lambda: I.random_smooth((30, 20, 64), seed=38, bc=(1, 1, 0))),
+                 ("blast", lambda: I.blast3d(48))]
+
+
 @pytest.mark.parametrize("case", PAIR_CASES, ids=[c[0] for c in PAIR_CASES])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_ct_z_pair_in_one_launch(mhd, case, prec):
     """The two CT_z operators that meet in the middle of a step, in one launch (op 2): the
     same bits as two single CT_z launches, and the oracle's two CT_z within tolerance."""
-    prob = case[1]()
+    _pair_case(mhd, case[1](), 2, prec)
+
+
+@pytest.mark.parametrize("case", PAIR_CASES_XY, ids=[c[0] for c in PAIR_CASES_XY])
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_ct_xy_pair_in_one_launch(mhd, case, axis, prec):
+    """The same for the x and y CT pairs (the shared-row two-pass march)."""
+    _pair_case(mhd, case[1](), axis, prec)
+
+
+def _pair_case(mhd, prob, axis, prec):
     p = mhd.FP64 if prec == "fp64" else mhd.FP32
     ref = oracle.Oracle.from_problem(prob)
     dt = 0.5 * ref.dt()
-    ref.ct(2, dt)
-    ref.ct(2, dt)
+    ref.ct(axis, dt)
+    ref.ct(axis, dt)
     got = []
     for ops in ((1, 1), (2,)):
         with mhd.Solver.from_problem(prob, prec=p) as s:
             for op in ops:
-                s.apply(op, 2, dt)
+                s.apply(op, axis, dt)
             got.append(s.read())
     assert np.array_equal(got[0], got[1]), np.abs(got[0] - got[1]).max()
     err = rel_l1(got[1], ref.f)
