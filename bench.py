@@ -45,18 +45,17 @@ STEP_ALG_BYTES = 384
 # DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
 # a step) from ncu captures on a 256^3 grid (the ncu summaries under profiles/), keyed by the
 # hash of the kernel sources they were taken on; another hash reports null.
-NCU_TRAFFIC_PER_CELL = {"5fc818fba809cbc8": 50.66}
+NCU_TRAFFIC_PER_CELL = {"609a66e66fd895eb": 50.77}
 # thread instructions per cell of one launch of each sweep kernel (ncu
-# smsp__thread_inst_executed.sum / cells, 256^3, the variants that do not reduce c_max),
-# keyed like the traffic: the sweeps are bound by instruction issue, and this gives the
-# issue rate they reach beside the HBM roofline
-NCU_INSTR_PER_CELL = {"5fc818fba809cbc8": {"fluid_x": 319.2, "fluid_y": 319.2,
-                                           "fluid_z": 381.5, "ct_x": 199.5, "ct_y": 199.5,
-                                           "ct_z": 286.7}}
+# smsp__thread_inst_executed.sum / cells, 256^3; one launch in six of each axis's fluid sweeps
+# also reduces c_max and is weighted in), keyed like the traffic: the sweeps are bound by
+# instruction issue, and this gives the issue rate they reach beside the HBM roofline
+NCU_INSTR_PER_CELL = {"609a66e66fd895eb": {"fluid_x": 325.0, "fluid_y": 325.0, "fluid_z": 391.6,
+                                           "ct_x": 184.4, "ct_y": 184.4, "ct_z": 285.2}}
 
 
 KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.cuh",
-                  "mhd_launch_impl.cuh")
+                  "mhd_tma.cuh", "mhd_launch_impl.cuh")
 
 
 def issue_object(dom: str, prof: dict, ipc: dict | None, cells: int, sms: int,

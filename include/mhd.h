@@ -163,7 +163,10 @@ mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int c
 /* Enqueue nsteps steps of every context of the batch as one persistent launch, ordered
  * after each context's pending work; each context's later work waits for it.  The work
  * list and the graph are cached per (nsteps, phases); with nsteps a multiple of 3 every
- * call reuses them.  Returns MHD_ERR_INVALID if a context's buffers moved since creation. */
+ * call reuses them.  Contexts may also be stepped alone between batch launches: a context
+ * whose buffers moved (mhd_step runs the middle CT pair of some steps as one launch, which
+ * swaps the B buffers; mhd_apply) has its operations rebuilt, after the batch's previous
+ * launch completed.  The batched steps run the middle pair as two launches, the same bits. */
 mhd_status mhd_batch_step(mhd_batch* b, int nsteps);
 
 /* As mhd_batch_step, with a step count per context: nsteps[i] >= 0 for each of the n
@@ -171,8 +174,8 @@ mhd_status mhd_batch_step(mhd_batch* b, int nsteps);
  * is.  Work items are queued step by step, so a context with more steps keeps advancing
  * after the others have finished within the same launch.  Used by a scheduler that gives
  * small grids many steps and large grids few in one launch.  The work list and graph are
- * cached for the last (counts, phases) key only.  MHD_ERR_INVALID for a negative count,
- * all counts 0, or moved buffers. */
+ * cached for the last (counts, phases) key only.  MHD_ERR_INVALID for a negative count or
+ * all counts 0. */
 mhd_status mhd_batch_step_each(mhd_batch* b, const int* nsteps);
 
 /* Wait for the batch.  MHD_ERR_TIMEOUT if a bounded device wait gave up (the launch then
@@ -247,8 +250,9 @@ mhd_status mhd_vis_range(mhd_ctx* ctx, int quantity, double* vmin, double* vmax)
  * n > MHD_SUMS_NOALLOC_MAX_CELLS (the scratch holds one row of partial sums per 65,536
  * cells, 4096 rows); MHD_ERR_CUDA if a CUDA call fails.  The first call on a device looks
  * up the scratch array's device address with that device current; make that first call
- * before any stream capture.  All calls share the one scratch array: calls whose work
- * overlaps on the GPU race, so serialise them. */
+ * before any stream capture.  The address is kept for the life of the process: a
+ * cudaDeviceReset of that device makes it stale.  All calls share the one scratch array:
+ * calls whose work overlaps on the GPU race, so serialise them. */
 #define MHD_SUMS_NOALLOC_MAX_CELLS 268435456LL
 mhd_status mhd_sums_noalloc(const void* const f[8], int dtype, long long n, double out[8],
                             void* stream);

@@ -421,15 +421,30 @@ static mhd_status batch_step_counts(mhd_batch* b, const int* nsteps) {
   const int n = (int)b->ctx.size();
   int smax = 0;
   std::vector<int> key;
+  bool ops_changed = false;
   for (int i = 0; i < n; ++i) {
     mhd_ctx* c = b->ctx[i];
     if (nsteps[i] < 0) return MHD_ERR_INVALID;
-    if (ctx_sig(c) != b->sig[i]) return MHD_ERR_INVALID;   // buffers moved (mhd_apply)
+    if (ctx_sig(c) != b->sig[i]) {
+      // the context's buffers moved since its operations were built (steps run alone,
+      // whose middle CT pair flips the B buffers, or mhd_apply): rebuild them; the work
+      // list and the captured graphs refer to operations by index and stay valid
+      b->sig[i] = ctx_sig(c);
+      for (int p = 0; p < 3; ++p)
+        build_step_ops(c, p, b->wpt, &b->ops[((size_t)i * 3 + p) * kOpsPerStep]);
+      ops_changed = true;
+    }
     smax = nsteps[i] > smax ? nsteps[i] : smax;
     key.push_back(nsteps[i]);
     key.push_back(c->phase);
   }
   if (smax < 1) return MHD_ERR_INVALID;
+  if (ops_changed) {
+    // a launch in flight may still read the operations
+    BK(cudaStreamSynchronize(b->stream), "synchronize before updating the operations");
+    BK(cudaMemcpy(b->d_ops, b->ops.data(), sizeof(BatchOp) * b->ops.size(),
+                  cudaMemcpyHostToDevice), "operations upload");
+  }
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
     // the previous launch may still read the current work list: let it finish first

@@ -97,3 +97,28 @@ def test_bounded_wait_times_out(mhd):
     # the device is still usable afterwards
     with mhd.Solver.from_problem(I.random_smooth((10, 10, 10), seed=4), prec=mhd.FP32) as s:
         s.step(2, sync=True)
+
+
+def test_batch_after_steps_alone(mhd):
+    """Contexts stepped alone between batch launches (the single-grid steps run the middle
+    CT pair in one launch, which swaps the B buffers; mhd_apply moves buffers too): the batch
+    rebuilds their operations, and the result equals the same steps all taken alone."""
+    probs = [I.batched_instance(i, lo=16, hi=40) for i in range(3)] + [I.blast3d(48)]
+    alone = []
+    for p in probs:
+        with mhd.Solver.from_problem(p, prec=mhd.FP32) as s:
+            s.step(3 + 4 + 2 + 3, sync=True)
+            alone.append(s.read())
+    solvers = [mhd.Solver.from_problem(p, prec=mhd.FP32) for p in probs]
+    with mhd.Batch(solvers) as b:
+        b.step(3)
+        for s in solvers:
+            s.step(4, sync=True)             # alone: buffers move
+        b.step(2)
+        assert b.sync() == mhd.MHD_OK
+        for s in solvers:
+            s.step(3, sync=True)
+    for s, ref in zip(solvers, alone):
+        assert s.state()[2] == 12
+        assert np.array_equal(s.read(), ref)
+        s.close()
