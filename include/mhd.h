@@ -178,9 +178,41 @@ mhd_status mhd_batch_step(mhd_batch* b, int nsteps);
  * all counts 0. */
 mhd_status mhd_batch_step_each(mhd_batch* b, const int* nsteps);
 
-/* Wait for the batch.  MHD_ERR_TIMEOUT if a bounded device wait gave up (the launch then
- * stops early and the contexts' states are incomplete). */
+/* Wait for the batch.  MHD_ERR_TIMEOUT if a bounded device wait gave up: the launch then
+ * stops early, the states of the contexts it advanced are incomplete, and each of those
+ * contexts reports MHD_ERR_TIMEOUT from then on (mhd_step, mhd_read, ...) until it is
+ * initialised again. */
 mhd_status mhd_batch_sync(mhd_batch* b);
+
+/* Launch shape of one context inside a batch.  Every field at 0 takes the default.  The
+ * shapes change speed only: each choice gives the same bits as mhd_step.
+ *   march_len  cells per work item along an x or y sweep (fluid and CT marching tiles,
+ *              each with its halo of 6 or 8 cells recomputed): 128, 192 or 256 (0: 192)
+ *   ct_march   1: x/y constrained transport as one marching pipeline per pencil, 0: with
+ *              EMF rows shared between neighbouring pencils where the grid allows it
+ *              (z extent >= 48 and at least 4 rows across)
+ *   seg_k      z sweeps: cells per lane of a warp segment, 2 or 3 (0: from the z extent)
+ *   z_warps    z sweeps: warp segments per work item, 1 .. 2^20 (0: the batch's
+ *              z_tile_warps)
+ *   alone      1: advance this context with the single-grid kernels (mhd_step, on the
+ *              context's own stream) instead of inside the persistent launch */
+typedef struct mhd_batch_shape {
+  int march_len;
+  int ct_march;
+  int seg_k;
+  int z_warps;
+  int alone;
+} mhd_batch_shape;
+
+/* Set the launch shapes of a batch: threads per CTA of the persistent kernel (128 or 256;
+ * the EMF rows of a shared-row CT tile are its warps; 0 keeps the current, initially 128),
+ * resident CTAs per SM (0: as many as fit), the bound of each device wait in SM clock
+ * cycles (1 .. 4e9; 0: 4e9, about 2 s) and, when shapes is not NULL, one mhd_batch_shape per
+ * context in creation order (NULL: every context at the defaults).  Waits for the batch's
+ * previous launch, rebuilds the work lists and drops the captured graphs.  MHD_ERR_INVALID
+ * for a value out of range (nothing is changed then). */
+mhd_status mhd_batch_configure(mhd_batch* b, int threads_per_cta, int ctas_per_sm,
+                               long long spin_cycles, const mhd_batch_shape* shapes);
 
 /* Resident CTAs of the persistent launch, work items per launch (0 before a step) and the
  * cudaStream_t the batch runs on (any pointer may be NULL). */

@@ -30,7 +30,10 @@ UNITS = [
     ("mhd_capi.cu", []),
     ("mhd_noalloc.cu", []),
     # the batched persistent kernel runs the FP32 sweep bodies: same flags as their TU
+    # (one unit per threads-per-CTA instantiation, compiled in parallel)
     ("mhd_batch.cu", FP32_FLAGS),
+    ("mhd_batch_nt128.cu", FP32_FLAGS),
+    ("mhd_batch_nt256.cu", FP32_FLAGS),
     ("mhd_vis.cu", []),
 ]
 

@@ -5,15 +5,12 @@
 // that small grids fill the GPU together.  An item of operation k of an instance may start
 // only when every item of that instance's earlier operations is complete: each instance
 // has a completion counter, incremented with release semantics after an item and awaited
-// with acquire semantics (bounded: after kSpinCycles the kernel records MHD_ERR_TIMEOUT,
+// with acquire semantics (bounded: after the spin limit the kernel records MHD_ERR_TIMEOUT,
 // raises an abort flag that every CTA checks, and returns instead of hanging).
 //
-// The operations are those of one method step (Sect. 4.2, Eq. "eq:L_sequence"): dt from
-// the previous step's c_max, then the forward and reverse sweeps of the instance's phase.
-// Every tile runs the same device bodies as the standalone kernels (FP32), so each grid's
-// result is bit-identical to advancing it alone with mhd_step.  Loads inside the
-// persistent launch use coherent paths (no read-only cache), because the buffers are
-// rewritten by other CTAs during the launch.
+// Each context has a launch shape (mhd_batch_shape: tile length of the x/y marches, CT form,
+// z segment length and items, or a route through the single-grid kernels); the kernel runs
+// at 128 or 256 threads per CTA (mhd_batch.cuh).  Shapes change speed, never bits.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -23,211 +20,35 @@
 #include <cuda_runtime.h>
 
 #include "../../include/mhd.h"
+#include "mhd_batch.cuh"
 #include "mhd_ctx.h"
-#include "mhd_flat.cuh"
-#include "mhd_march.cuh"
-#include "mhd_segz.cuh"
 
-namespace mhd {
-
-constexpr int kBatchNT = 128;     // threads per CTA (all bodies use 128)
-constexpr int kBatchS = kMarchS;  // march tile length along the sweep (as the single-grid kernels)
-constexpr int kBatchK = 3;        // cells per lane of the z segments (or 2, seg_k_for)
-constexpr long long kSpinCycles = 4000000000LL;   // ~2 s of SM clock per wait
-constexpr int kFlatCells = kBatchNT * 16;   // cells per item of the per-cell operations
-constexpr long long kAutoTiles = 1024;      // target items per z sweep when not set
-// OP_NOP: a fluid sweep along a flat axis (identity, no items); OP_CMAX: c_max of the state
-// (the last fluid sweep of a step along a flat axis); OP_CTFLAT: CT along a flat axis
-enum : int { OP_DT = 0, OP_FLUID = 1, OP_CT = 2, OP_NOP = 3, OP_CMAX = 4, OP_CTFLAT = 5 };
-
-constexpr int kBatchRowsR = kBatchNT / 32;   // warps of a shared-row CT tile
-
-struct BatchOp {
-  FieldSet<float> in, out;
-  GridDesc g;
-  int kind, axis, last;
-  int rows;            // CT x/y in the shared-row form (ct_rows_xy_tile)
-  int segk;            // z segments: cells per lane (2 or 3, seg_k_for)
-  int gx;              // march: tiles across the transverse plane (tile = by * gx + bx)
-  int wpt;             // z segments: warp segments per tile
-  long long nwarps;    // z segments: warp segments of the sweep
-  int tiles;
-};
-struct BatchItem {
-  int inst, op, tile, need;
-};
-struct BatchInst {
-  DevScalars* ds;
-  float gamma;
-  double h, cfl_h;
-};
-struct BatchArgs {
-  const BatchItem* items;
-  long long nitems;
-  const BatchOp* ops;
-  const BatchInst* inst;
-  unsigned long long* queue;
-  int* done;
-  int* abort;
-  int* status;
-  long long spin_limit;
-};
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ int ld_relaxed(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-template <int A>
-__device__ __forceinline__ void batch_fluid_xy(const BatchOp& op, const BatchInst& in,
-                                               unsigned tile, unsigned char* smem) {
-  const unsigned bx = tile % op.gx, by = tile / op.gx;
-  if (op.last)
-    fluid_march_xy_tile<float, A, true, false, kBatchS, kBatchNT>(op.g, op.in, op.out, in.gamma,
-                                                                  in.h, in.ds, bx, by, smem);
-  else
-    fluid_march_xy_tile<float, A, false, false, kBatchS, kBatchNT>(op.g, op.in, op.out, in.gamma,
-                                                                   in.h, in.ds, bx, by, smem);
-}
-
-template <int A>
-__device__ __forceinline__ void batch_ct_xy(const BatchOp& op, const BatchInst& in, unsigned tile,
-                                            unsigned char* smem) {
-  const unsigned bx = tile % op.gx, by = tile / op.gx;
-  if (op.rows)
-    ct_rows_xy_tile<float, A, kBatchS, kBatchRowsR>(op.g, op.in, op.out, in.h, in.ds, bx, by,
-                                                    smem);
-  else
-    ct_march_xy_tile<float, A, kBatchS, kBatchNT>(op.g, op.in, op.out, in.h, in.ds, bx, by, smem);
-}
-
-// 4 resident CTAs per SM (a 128-register cap, with a few bytes of spill) measured 10%
-// faster than 3 on the 64-instance batched workload
-#ifndef MHD_BATCH_MINB
-#define MHD_BATCH_MINB 4
-#endif
-__global__ void __launch_bounds__(kBatchNT, MHD_BATCH_MINB) batch_kernel(BatchArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ long long s_id;
-  __shared__ int s_go;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const long long id = (long long)atomicAdd(a.queue, 1ull);
-      int go = id < a.nitems ? 1 : 0;
-      if (go) {
-        const BatchItem it = a.items[id];
-        // poll with relaxed loads (cheaper than GPU-scope acquire loads, which must order
-        // every later load of the SM), then one acquire load once the count is reached: it
-        // reads a value of the counter's release sequence
-        if (ld_acquire(a.done + it.inst) < it.need) {
-          const long long t0 = clock64();
-          while (ld_relaxed(a.done + it.inst) < it.need) {
-            if (ld_relaxed(a.abort)) { go = 0; break; }
-            if (clock64() - t0 > a.spin_limit) {
-              atomicOr(a.status, 1);
-              atomicExch(a.abort, 1);
-              go = 0;
-              break;
-            }
-            __nanosleep(64);
-          }
-          if (go) (void)ld_acquire(a.done + it.inst);
-        }
-      }
-      s_id = id;
-      s_go = go;
-    }
-    __syncthreads();
-    if (!s_go) break;
-    const BatchItem it = a.items[s_id];
-    const BatchOp& op = a.ops[it.op];
-    const BatchInst& ins = a.inst[it.inst];
-    const int warp = threadIdx.x >> 5;
-    if (op.kind == OP_DT) {
-      if (threadIdx.x == 0) dt_update<float>(ins.ds, ins.cfl_h);
-    } else if (op.kind == OP_CMAX || op.kind == OP_CTFLAT) {
-      const long long N = (long long)op.g.n[0] * op.g.n[1] * op.g.n[2];
-      const long long i0 = (long long)it.tile * kFlatCells;
-      const long long i1 = min(i0 + kFlatCells, N);
-      if (op.kind == OP_CMAX) {
-        cmax_range<float, false>(op.g, op.in, ins.gamma, ins.ds, i0 + threadIdx.x, i1, kBatchNT);
-      } else {
-        const float dth = (float)(ins.ds->dt / ins.h);
-        int st;
-        if (op.axis == 0)
-          st = ct_flat_range<float, 0>(op.g, op.in, op.out, dth, i0 + threadIdx.x, i1, kBatchNT);
-        else if (op.axis == 1)
-          st = ct_flat_range<float, 1>(op.g, op.in, op.out, dth, i0 + threadIdx.x, i1, kBatchNT);
-        else
-          st = ct_flat_range<float, 2>(op.g, op.in, op.out, dth, i0 + threadIdx.x, i1, kBatchNT);
-        if (st) atomicOr(&ins.ds->status, st);
-      }
-    } else if (op.axis < 2) {
-      if (op.kind == OP_FLUID) {
-        if (op.axis == 0) batch_fluid_xy<0>(op, ins, it.tile, smem_raw);
-        else batch_fluid_xy<1>(op, ins, it.tile, smem_raw);
-      } else {
-        if (op.axis == 0) batch_ct_xy<0>(op, ins, it.tile, smem_raw);
-        else batch_ct_xy<1>(op, ins, it.tile, smem_raw);
-      }
-    } else {
-      const long long w0 = (long long)it.tile * op.wpt;
-      const long long w1 = min(w0 + op.wpt, op.nwarps);
-      for (long long w = w0 + warp; w < w1; w += kBatchNT / 32) {
-        if (op.segk == 2) {
-          if (op.kind == OP_FLUID) {
-            if (op.last)
-              fluid_seg_z_warp<float, true, false, 2, false>(op.g, op.in, op.out, ins.gamma, ins.h,
-                                                             ins.ds, w);
-            else
-              fluid_seg_z_warp<float, false, false, 2, false>(op.g, op.in, op.out, ins.gamma,
-                                                              ins.h, ins.ds, w);
-          } else {
-            ct_seg_z_warp<float, 2, false>(op.g, op.in, op.out, ins.h, ins.ds, w);
-          }
-        } else {
-          if (op.kind == OP_FLUID) {
-            if (op.last)
-              fluid_seg_z_warp<float, true, false, kBatchK, false>(op.g, op.in, op.out, ins.gamma,
-                                                                   ins.h, ins.ds, w);
-            else
-              fluid_seg_z_warp<float, false, false, kBatchK, false>(op.g, op.in, op.out,
-                                                                    ins.gamma, ins.h, ins.ds, w);
-          } else {
-            ct_seg_z_warp<float, kBatchK, false>(op.g, op.in, op.out, ins.h, ins.ds, w);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(a.done + it.inst, 1);
-    }
-  }
-}
-
-}  // namespace mhd
 
 using mhd::BatchArgs;
 using mhd::BatchInst;
 using mhd::BatchItem;
 using mhd::BatchOp;
 
+// a context's launch shape with its defaults resolved (mhd_batch_shape)
+struct BatchShape {
+  int s = mhd::kMarchS == 128 || mhd::kMarchS == 256 ? mhd::kMarchS : 192;
+  int rows = 1;       // shared-row CT where the grid allows it
+  int segk = 0;       // 0: seg_k_for(nz)
+  int wpt = 0;        // 0: the batch's z_tile_warps
+  int alone = 0;
+};
+
 struct mhd_batch {
   std::vector<mhd_ctx*> ctx;
   std::vector<unsigned> sig;           // buffer state of each context when its ops were built
+  std::vector<BatchShape> shape;
   std::vector<BatchOp> ops;            // [instance][phase][13]
+  const mhd::BatchKernel* kern = nullptr;
   cudaStream_t stream = nullptr;
   int grid = 0;                        // resident CTAs of the persistent launch
+  int ctas_per_sm = 0;                 // asked for (0: as many as fit)
   int wpt = 0;                         // z warp segments per tile (0: chosen per sweep)
-  size_t smem = 0;
+  long long spin = mhd::kSpinCycles;
   BatchOp* d_ops = nullptr;
   BatchInst* d_inst = nullptr;
   BatchItem* d_items = nullptr;
@@ -237,9 +58,9 @@ struct mhd_batch {
   int* d_abort = nullptr;              // d_abort[0] abort flag, d_abort[1] status
   int* h_status = nullptr;             // pinned
   cudaEvent_t ev = nullptr;
-  // graph per (nsteps, phases of the instances); items uploaded for the same key
+  // graph per (step counts, phases of the instances); items uploaded for the same key
   std::map<std::vector<int>, std::pair<cudaGraphExec_t, long long>> graphs;
-  std::vector<int> items_key;
+  std::vector<char> in_last;           // contexts in a persistent launch since the last sync
   std::string err;
 };
 
@@ -262,10 +83,14 @@ static unsigned ctx_sig(const mhd_ctx* c) {
 }
 
 // the 13 operations of one step at `phase`, in launch order, with the buffers they read
-// and write (mirrors enqueue_step_t in mhd_capi.cu)
-static void build_step_ops(const mhd_ctx* c, int phase, int wpt, BatchOp* out) {
+// and write (mirrors enqueue_step_t in mhd_capi.cu), tiled for NT threads per CTA
+static void build_step_ops(const mhd_ctx* c, int phase, int bwpt, const BatchShape& sh, int nt,
+                           BatchOp* out) {
   int cur[8];
   for (int k = 0; k < 8; ++k) cur[k] = c->cur[k];
+  const int R = nt / 32;                 // EMF rows of a shared-row CT tile
+  const int flat_cells = nt * mhd::kFlatPerThread;
+  const int wpt = sh.wpt > 0 ? sh.wpt : bwpt;
   auto fs = [&](bool other) {
     FieldSet<float> f;
     for (int k = 0; k < 8; ++k) f.f[k] = (float*)c->buf[other ? 1 - cur[k] : cur[k]][k];
@@ -276,19 +101,19 @@ static void build_step_ops(const mhd_ctx* c, int phase, int wpt, BatchOp* out) {
     if (op.axis < 2) {
       const int o = op.axis == 0 ? 1 : 0;
       const long long np = (long long)g.n[2] * g.n[o];
-      op.rows = (op.kind == mhd::OP_CT && mhd::ct_use_rows(g, op.axis)) ? 1 : 0;
-      op.gx = op.rows ? ((g.n[2] + 30) / 31) * ((g.n[o] + mhd::kBatchRowsR - 2) /
-                                                (mhd::kBatchRowsR - 1))
-                      : (int)((np + mhd::kBatchNT - 1) / mhd::kBatchNT);
-      op.tiles = op.gx * ((g.n[op.axis] + mhd::kBatchS - 1) / mhd::kBatchS);
+      op.s = sh.s;
+      op.rows = (op.kind == mhd::OP_CT && sh.rows && mhd::ct_use_rows(g, op.axis)) ? 1 : 0;
+      op.gx = op.rows ? ((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1))
+                      : (int)((np + nt - 1) / nt);
+      op.tiles = op.gx * ((g.n[op.axis] + op.s - 1) / op.s);
     } else {
-      op.segk = mhd::seg_k_for(g.n[2]);
+      op.segk = sh.segk ? sh.segk : mhd::seg_k_for(g.n[2]);
       const int seg = 32 * op.segk - (op.kind == mhd::OP_FLUID ? 6 : 8);
       op.nwarps = (long long)g.n[0] * g.n[1] * ((g.n[2] + seg - 1) / seg);
       // 0: about kAutoTiles items per z sweep (small grids get short items, large ones
       // up to 128 warp segments each)
       long long w = wpt > 0 ? wpt : (op.nwarps + mhd::kAutoTiles - 1) / mhd::kAutoTiles;
-      w = w < 4 ? 4 : (w > 128 && wpt == 0 ? 128 : w);
+      if (wpt == 0) w = w < 4 ? 4 : (w > 128 ? 128 : w);
       op.wpt = (int)w;
       op.tiles = (int)((op.nwarps + w - 1) / w);
     }
@@ -304,7 +129,7 @@ static void build_step_ops(const mhd_ctx* c, int phase, int wpt, BatchOp* out) {
     op.in = fs(false);
     op.out = fs(true);
     const long long ncell = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
-    const int flat_tiles = (int)((ncell + mhd::kFlatCells - 1) / mhd::kFlatCells);
+    const int flat_tiles = (int)((ncell + flat_cells - 1) / flat_cells);
     if (kind == mhd::OP_DT) {
       op.tiles = 1;
     } else if (mhd::axis_is_flat(c->g, axis)) {
@@ -337,13 +162,41 @@ static void build_step_ops(const mhd_ctx* c, int phase, int wpt, BatchOp* out) {
   }
 }
 
+static void build_ops(mhd_batch* b, int i) {
+  b->sig[i] = ctx_sig(b->ctx[i]);
+  for (int p = 0; p < 3; ++p)
+    build_step_ops(b->ctx[i], p, b->wpt, b->shape[i], b->kern->nt,
+                   &b->ops[((size_t)i * 3 + p) * kOpsPerStep]);
+}
+
+static void drop_graphs(mhd_batch* b) {
+  for (auto& kv : b->graphs)
+    if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
+  b->graphs.clear();
+}
+
+// the persistent kernel's resident CTAs for the batch's kernel and CTAs-per-SM request
+static mhd_status set_grid(mhd_batch* b) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaError_t e = b->kern->prepare(&per_sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bfail(b, e, "batch kernel setup");
+  if (per_sm < 1) {
+    b->err = "batch kernel: no resident CTA fits";
+    return MHD_ERR_CUDA;
+  }
+  if (b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm) per_sm = b->ctas_per_sm;
+  b->grid = per_sm * sms;   // every CTA resident: no item waits on a CTA that cannot run
+  return MHD_OK;
+}
+
 extern "C" {
 
 void mhd_batch_destroy(mhd_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
-  for (auto& kv : b->graphs)
-    if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
+  drop_graphs(b);
   cudaFree(b->d_ops);
   cudaFree(b->d_inst);
   cudaFree(b->d_items);
@@ -365,15 +218,15 @@ mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int c
     if (!c || c->esz != 4 || c->cfg.fp64_pressure) return MHD_ERR_INVALID;
   }
   mhd_batch* b = new mhd_batch();
+  b->kern = &mhd::batch_kernel_nt128();
   b->wpt = z_tile_warps > 0 ? z_tile_warps : 0;
+  b->ctas_per_sm = ctas_per_sm > 0 ? ctas_per_sm : 0;
   b->ctx.assign(ctxs, ctxs + n);
   b->sig.resize(n);
+  b->shape.resize(n);
+  b->in_last.assign(n, 0);
   b->ops.resize((size_t)n * 3 * kOpsPerStep);
-  for (int i = 0; i < n; ++i) {
-    b->sig[i] = ctx_sig(ctxs[i]);
-    for (int p = 0; p < 3; ++p)
-      build_step_ops(ctxs[i], p, b->wpt, &b->ops[((size_t)i * 3 + p) * kOpsPerStep]);
-  }
+  for (int i = 0; i < n; ++i) build_ops(b, i);
   std::vector<BatchInst> inst(n);
   for (int i = 0; i < n; ++i) {
     inst[i].ds = ctxs[i]->ds;
@@ -395,50 +248,91 @@ mhd_status mhd_batch_create(mhd_ctx* const* ctxs, int n, int z_tile_warps, int c
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_inst, inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_abort, 0, sizeof(int) * 2);
-  // shared memory: the largest tile body (the per-element CT march's prefetch ring, 15 values
-  // per iteration, or the 16-byte fluid staging)
-  b->smem = std::max({sizeof(float) * (size_t)mhd::kMarchRing * 15 * mhd::kBatchNT,
-                      mhd::march_tile_smem<float>(), mhd::ct_rows_smem<float>(mhd::kBatchRowsR)});
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mhd::batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)b->smem);
-  int per_sm = 0, dev = 0, sms = 0;
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mhd::batch_kernel, mhd::kBatchNT,
-                                                      b->smem);
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess || per_sm < 1) { bfail(b, e, "batch setup"); return fail(MHD_ERR_CUDA); }
-  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-  b->grid = per_sm * sms;   // every CTA resident: no item waits on a CTA that cannot run
+  if (e != cudaSuccess) { bfail(b, e, "batch setup"); return fail(MHD_ERR_CUDA); }
+  const mhd_status gs = set_grid(b);
+  if (gs != MHD_OK) return fail(gs);
   *out = b;
   return MHD_OK;
 }
 
-// Advance every instance by nsteps steps in one persistent launch.
-// One persistent launch advancing instance i by nsteps[i] steps (0 leaves it as it is).
+mhd_status mhd_batch_configure(mhd_batch* b, int threads_per_cta, int ctas_per_sm,
+                               long long spin_cycles, const mhd_batch_shape* shapes) {
+  if (!b) return MHD_ERR_INVALID;
+  if (threads_per_cta != 0 && threads_per_cta != 128 && threads_per_cta != 256)
+    return MHD_ERR_INVALID;
+  if (ctas_per_sm < 0 || spin_cycles < 0 || spin_cycles > mhd::kSpinCycles) return MHD_ERR_INVALID;
+  const int n = (int)b->ctx.size();
+  std::vector<BatchShape> sh(n);
+  for (int i = 0; shapes && i < n; ++i) {
+    const mhd_batch_shape& q = shapes[i];
+    if ((q.march_len != 0 && !mhd::batch_len_ok(q.march_len)) || q.ct_march < 0 ||
+        q.ct_march > 1 || (q.seg_k != 0 && q.seg_k != 2 && q.seg_k != 3) || q.z_warps < 0 ||
+        q.z_warps > (1 << 20) || q.alone < 0 || q.alone > 1)
+      return MHD_ERR_INVALID;
+    if (q.march_len) sh[i].s = q.march_len;
+    sh[i].rows = q.ct_march ? 0 : 1;
+    sh[i].segk = q.seg_k;
+    sh[i].wpt = q.z_warps;
+    sh[i].alone = q.alone;
+  }
+  // the previous launch may still read the operations and the work list
+  BK(cudaStreamSynchronize(b->stream), "synchronize before reconfiguring");
+  drop_graphs(b);
+  if (threads_per_cta) {
+    b->kern = threads_per_cta == 256 ? &mhd::batch_kernel_nt256() : &mhd::batch_kernel_nt128();
+  }
+  b->ctas_per_sm = ctas_per_sm;
+  b->spin = spin_cycles > 0 ? spin_cycles : mhd::kSpinCycles;
+  b->shape = sh;
+  for (int i = 0; i < n; ++i) build_ops(b, i);
+  BK(cudaMemcpy(b->d_ops, b->ops.data(), sizeof(BatchOp) * b->ops.size(), cudaMemcpyHostToDevice),
+     "operations upload");
+  return set_grid(b);
+}
+
+// One persistent launch advancing instance i by nsteps[i] steps (0 leaves it as it is);
+// contexts routed alone step through mhd_step on their own streams instead.
 static mhd_status batch_step_counts(mhd_batch* b, const int* nsteps) {
   const int n = (int)b->ctx.size();
-  int smax = 0;
+  int smax = 0, pmax = 0;
   std::vector<int> key;
   bool ops_changed = false;
   for (int i = 0; i < n; ++i) {
-    mhd_ctx* c = b->ctx[i];
     if (nsteps[i] < 0) return MHD_ERR_INVALID;
-    if (ctx_sig(c) != b->sig[i]) {
+    smax = nsteps[i] > smax ? nsteps[i] : smax;
+  }
+  if (smax < 1) return MHD_ERR_INVALID;
+  for (int i = 0; i < n; ++i) {
+    mhd_ctx* c = b->ctx[i];
+    const int k = b->shape[i].alone ? 0 : nsteps[i];
+    if (k > 0 && ctx_sig(c) != b->sig[i]) {
       // the context's buffers moved since its operations were built (steps run alone,
       // whose middle CT pair flips the B buffers, or mhd_apply): rebuild them; the work
       // list and the captured graphs refer to operations by index and stay valid
-      b->sig[i] = ctx_sig(c);
-      for (int p = 0; p < 3; ++p)
-        build_step_ops(c, p, b->wpt, &b->ops[((size_t)i * 3 + p) * kOpsPerStep]);
+      build_ops(b, i);
       ops_changed = true;
     }
-    smax = nsteps[i] > smax ? nsteps[i] : smax;
-    key.push_back(nsteps[i]);
-    key.push_back(c->phase);
+    pmax = k > pmax ? k : pmax;
+    key.push_back(k);
+    key.push_back(k > 0 ? c->phase : 0);
   }
-  if (smax < 1) return MHD_ERR_INVALID;
+  // contexts routed through the single-grid kernels
+  for (int i = 0; i < n; ++i) {
+    if (!b->shape[i].alone || nsteps[i] == 0) continue;
+    // (a status the context already carries is its own to report, as in the launch)
+    const mhd_status st = mhd_step(b->ctx[i], nsteps[i], -1.0, nullptr, nullptr);
+    if (st != MHD_OK && st != MHD_ERR_UNPHYSICAL && st != MHD_ERR_TIMEOUT) return st;
+  }
+  if (pmax < 1) {
+    // nothing for the persistent kernel: the batch's stream still orders after the
+    // contexts' steps, so that mhd_batch_sync waits for them
+    for (int i = 0; i < n; ++i) {
+      if (!nsteps[i]) continue;
+      BK(cudaEventRecord(b->ev, b->ctx[i]->stream), "event");
+      BK(cudaStreamWaitEvent(b->stream, b->ev, 0), "wait event");
+    }
+    return MHD_OK;
+  }
   if (ops_changed) {
     // a launch in flight may still read the operations
     BK(cudaStreamSynchronize(b->stream), "synchronize before updating the operations");
@@ -452,10 +346,10 @@ static mhd_status batch_step_counts(mhd_batch* b, const int* nsteps) {
     // items: round by round (step, operation), all instances of a round together
     std::vector<BatchItem> items;
     std::vector<int> need(n, 0);
-    for (int s = 0; s < smax; ++s)
+    for (int s = 0; s < pmax; ++s)
       for (int k = 0; k < kOpsPerStep; ++k)
         for (int i = 0; i < n; ++i) {
-          if (s >= nsteps[i]) continue;
+          if (s >= key[2 * i]) continue;
           const int p = (b->ctx[i]->phase + s) % 3;
           const int opi = (i * 3 + p) * kOpsPerStep + k;
           const int tiles = b->ops[opi].tiles;
@@ -472,9 +366,7 @@ static mhd_status batch_step_counts(mhd_batch* b, const int* nsteps) {
     BK(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * nitems, cudaMemcpyHostToDevice),
        "items upload");
     // drop graphs that referenced another item list
-    for (auto& kv : b->graphs)
-      if (kv.second.first) cudaGraphExecDestroy(kv.second.first);
-    b->graphs.clear();
+    drop_graphs(b);
     BatchArgs args;
     args.items = b->d_items;
     args.nitems = nitems;
@@ -484,14 +376,13 @@ static mhd_status batch_step_counts(mhd_batch* b, const int* nsteps) {
     args.done = b->d_done;
     args.abort = b->d_abort;
     args.status = b->d_abort + 1;
-    args.spin_limit = mhd::kSpinCycles;
+    args.spin_limit = b->spin;
     cudaGraph_t gr = nullptr;
     BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), b->stream);
     cudaMemsetAsync(b->d_done, 0, sizeof(int) * n, b->stream);
     cudaMemsetAsync(b->d_abort, 0, sizeof(int), b->stream);   // abort flag; status is sticky
-    mhd::batch_kernel<<<b->grid, mhd::kBatchNT, b->smem, b->stream>>>(args);
-    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e1 = b->kern->launch(b->grid, b->stream, args);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &gr);
     if (e1 != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return bfail(b, e1, "capture"); }
     if (e2 != cudaSuccess) return bfail(b, e2, "end capture");
@@ -501,19 +392,30 @@ static mhd_status batch_step_counts(mhd_batch* b, const int* nsteps) {
     if (e3 != cudaSuccess) return bfail(b, e3, "instantiate");
     it = b->graphs.emplace(key, std::make_pair(ex, nitems)).first;
   }
-  // order after each context's pending work, run, and make each context wait for it
+  // order after each persistent context's pending work, run, and make each of them wait
+  // for the launch
   for (int i = 0; i < n; ++i) {
+    if (!key[2 * i]) continue;
     BK(cudaEventRecord(b->ev, b->ctx[i]->stream), "event");
     BK(cudaStreamWaitEvent(b->stream, b->ev, 0), "wait event");
   }
   BK(cudaGraphLaunch(it->second.first, b->stream), "batch launch");
   BK(cudaEventRecord(b->ev, b->stream), "event");
   for (int i = 0; i < n; ++i) {
+    if (!key[2 * i]) continue;
+    b->in_last[i] = 1;
     BK(cudaStreamWaitEvent(b->ctx[i]->stream, b->ev, 0), "wait event");
     mhd_ctx* c = b->ctx[i];
     c->phase = (c->phase + nsteps[i]) % 3;
     c->step += nsteps[i];
     c->steps_base += nsteps[i];
+  }
+  // the routed contexts' steps run beside the launch; the batch's stream then waits for
+  // them, so that mhd_batch_sync covers them
+  for (int i = 0; i < n; ++i) {
+    if (!b->shape[i].alone || !nsteps[i]) continue;
+    BK(cudaEventRecord(b->ev, b->ctx[i]->stream), "event");
+    BK(cudaStreamWaitEvent(b->stream, b->ev, 0), "wait event");
   }
   return MHD_OK;
 }
@@ -529,14 +431,20 @@ mhd_status mhd_batch_step_each(mhd_batch* b, const int* nsteps) {
   return batch_step_counts(b, nsteps);
 }
 
-// Wait for the batch's stream; MHD_ERR_TIMEOUT if a bounded wait gave up.
+// Wait for the batch's stream; MHD_ERR_TIMEOUT if a bounded wait gave up, and then every
+// context of the persistent launches since the last sync is marked (its later calls
+// report the timeout until it is initialised again).
 mhd_status mhd_batch_sync(mhd_batch* b) {
   if (!b) return MHD_ERR_INVALID;
   BK(cudaMemcpyAsync(b->h_status, b->d_abort, sizeof(int) * 2, cudaMemcpyDeviceToHost, b->stream),
      "status");
   BK(cudaStreamSynchronize(b->stream), "synchronize");
+  std::vector<char> launched(b->ctx.size(), 0);
+  launched.swap(b->in_last);
   if (!b->h_status[1]) return MHD_OK;
   BK(cudaMemset(b->d_abort + 1, 0, sizeof(int)), "status reset");   // reported once
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (launched[i]) b->ctx[i]->status |= mhd::ST_TIMEOUT;
   return MHD_ERR_TIMEOUT;
 }
 
@@ -545,7 +453,6 @@ mhd_status mhd_batch_sync(mhd_batch* b) {
 // MHD_ERR_TIMEOUT, leaving the device usable.
 mhd_status mhd_batch_selftest_timeout(long long spin_cycles) {
   if (spin_cycles < 1 || spin_cycles > mhd::kSpinCycles) return MHD_ERR_INVALID;
-  mhd_batch* b = nullptr;
   BatchItem item{0, 0, 0, 1};            // instance 0 waits for one completion: never comes
   BatchItem* d_item = nullptr;
   unsigned long long* d_queue = nullptr;
@@ -558,6 +465,9 @@ mhd_status mhd_batch_selftest_timeout(long long spin_cycles) {
   if (e == cudaSuccess) e = cudaMemcpy(d_item, &item, sizeof(item), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(d_queue, 0, sizeof(*d_queue));
   if (e == cudaSuccess) e = cudaMemset(d_words, 0, sizeof(int) * 3);
+  int per_sm = 0;
+  const mhd::BatchKernel& k = mhd::batch_kernel_nt128();
+  if (e == cudaSuccess) e = k.prepare(&per_sm);
   if (e == cudaSuccess) {
     BatchArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -568,8 +478,7 @@ mhd_status mhd_batch_selftest_timeout(long long spin_cycles) {
     a.abort = d_words + 1;
     a.status = d_words + 2;
     a.spin_limit = spin_cycles;
-    mhd::batch_kernel<<<1, mhd::kBatchNT, 0>>>(a);
-    e = cudaGetLastError();
+    e = k.launch(1, nullptr, a);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(h_words, d_words, sizeof(int) * 3, cudaMemcpyDeviceToHost);
   }
@@ -578,7 +487,6 @@ mhd_status mhd_batch_selftest_timeout(long long spin_cycles) {
   cudaFree(d_item);
   cudaFree(d_queue);
   cudaFree(d_words);
-  (void)b;
   return st;
 }
 

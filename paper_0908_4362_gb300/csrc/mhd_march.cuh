@@ -412,8 +412,8 @@ __host__ __device__ inline bool march_vec(const GridDesc& g) {
   return sizeof(T) == 4 && g.n[2] % 4 == 0;
 }
 template <typename T>
-static size_t march_tile_smem() {
-  return sizeof(T) * (size_t)kMarchRing * kVecRows * 128;   // both stagings: 10 values per cell
+static size_t march_tile_smem(int nt = 128) {
+  return sizeof(T) * (size_t)kMarchRing * kVecRows * nt;    // both stagings: 10 values per cell
 }
 
 template <typename T, int A, bool LAST, int PM, int S, int NT>
@@ -421,7 +421,7 @@ __device__ __forceinline__ void fluid_march_xy_tile(const GridDesc& g, const Fie
                                                     const FieldSet<T>& out, T gamma, double h,
                                                     DevScalars* ds, unsigned bx, unsigned by,
                                                     unsigned char* smem_raw) {
-  if constexpr (sizeof(T) == 4 && NT == 128) {
+  if constexpr (sizeof(T) == 4) {
     if (march_vec<T>(g)) {
       fluid_march_xy_tile_vec<A, LAST, PM, S, NT>(g, in, out, gamma, h, ds, bx, by, smem_raw);
       return;

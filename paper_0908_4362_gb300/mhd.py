@@ -27,7 +27,8 @@ EXPORTS = ("mhd_create", "mhd_init_fields", "mhd_upload", "mhd_step", "mhd_apply
            "mhd_info", "mhd_stream", "mhd_profile", "mhd_profile_read", "mhd_destroy",
            "mhd_status_str", "mhd_last_error", "mhd_sums_noalloc", "mhd_batch_create",
            "mhd_batch_step", "mhd_batch_step_each", "mhd_batch_sync", "mhd_batch_info",
-           "mhd_batch_destroy", "mhd_batch_selftest_timeout", "mhd_vis_curve",
+           "mhd_batch_destroy", "mhd_batch_selftest_timeout", "mhd_batch_configure",
+           "mhd_vis_curve",
            "mhd_vis_slice", "mhd_vis_volume", "mhd_vis_range")
 
 
@@ -35,6 +36,12 @@ class MhdConfig(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
                 ("gamma", C.c_double), ("cfl", C.c_double), ("bc", C.c_int * 3),
                 ("prec", C.c_int), ("fp64_pressure", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class BatchShape(C.Structure):
+    """mhd_batch_shape: launch shape of one context inside a batch (0 = default)."""
+    _fields_ = [("march_len", C.c_int), ("ct_march", C.c_int), ("seg_k", C.c_int),
+                ("z_warps", C.c_int), ("alone", C.c_int)]
 
 
 class MhdError(RuntimeError):
@@ -87,6 +94,8 @@ def load_library(path: str | None = None) -> C.CDLL:
         "mhd_batch_info": ([vp, ip, C.POINTER(C.c_longlong), C.POINTER(vp)], C.c_int),
         "mhd_batch_destroy": ([vp], None),
         "mhd_batch_selftest_timeout": ([C.c_longlong], C.c_int),
+        "mhd_batch_configure": ([vp, C.c_int, C.c_int, C.c_longlong, C.POINTER(BatchShape)],
+                                C.c_int),
         "mhd_status_str": ([C.c_int], C.c_char_p),
         "mhd_last_error": ([vp], C.c_char_p),
     }
@@ -346,6 +355,24 @@ class Batch:
 
     def sync(self) -> int:
         return self.lib.mhd_batch_sync(self.b)
+
+    def configure(self, threads_per_cta: int = 0, ctas_per_sm: int = 0, spin_cycles: int = 0,
+                  shapes=None):
+        """mhd_batch_configure.  shapes: None, or one dict (or BatchShape) per solver with
+        any of march_len, ct_march, seg_k, z_warps, alone (missing keys: 0 = default)."""
+        arr = None
+        if shapes is not None:
+            if len(shapes) != len(self.solvers):
+                raise ValueError("one shape per solver")
+            arr = (BatchShape * len(shapes))()
+            for a, sh in zip(arr, shapes):
+                for k, v in (sh.items() if isinstance(sh, dict) else
+                             ((f, getattr(sh, f)) for f, _ in BatchShape._fields_)):
+                    setattr(a, k, int(v))
+        st = self.lib.mhd_batch_configure(self.b, int(threads_per_cta), int(ctas_per_sm),
+                                          int(spin_cycles), arr)
+        if st != MHD_OK:
+            raise MhdError(st, f"mhd_batch_configure: {self.lib.mhd_status_str(st).decode()}")
 
     def info(self):
         c, n, s = C.c_int(), C.c_longlong(), C.c_void_p()

@@ -122,3 +122,93 @@ def test_batch_after_steps_alone(mhd):
         assert s.state()[2] == 12
         assert np.array_equal(s.read(), ref)
         s.close()
+
+
+def _shape_problems():
+    # _problems() plus grids whose x or y extent spans several marching tiles of every
+    # length (128, 192, 256) with a ragged last tile, with shared-row CT (z >= 48)
+    return _problems() + [I.random_smooth((300, 20, 52), seed=24, bc=(0, 0, 1)),
+                          I.random_smooth((16, 270, 48), seed=25, bc=(1, 0, 0)),
+                          I.batched_instance(7, lo=40, hi=140)]
+
+
+def _cycle(shapes, n):
+    return [dict(shapes[i % len(shapes)]) for i in range(n)]
+
+
+SHAPE_SETS = {
+    "nt256_default": (256, [{}]),
+    "len128_pencil_ct_k2": (128, [{"march_len": 128, "ct_march": 1, "seg_k": 2, "z_warps": 7}]),
+    "len256_k3_w1": (256, [{"march_len": 256, "seg_k": 3, "z_warps": 1}]),
+    "mixed_some_alone": (128, [{"march_len": 256}, {"alone": 1}, {"ct_march": 1, "seg_k": 3},
+                               {"march_len": 128, "z_warps": 64}, {"alone": 1, "march_len": 128}]),
+}
+
+
+@pytest.mark.parametrize("name", list(SHAPE_SETS))
+def test_batch_shapes_bitwise(mhd, name):
+    """Every launch shape (threads per CTA, marching tile length, CT form, z segment length
+    and items, the route through the single-grid kernels) gives the same bits as mhd_step."""
+    nt, shapes = SHAPE_SETS[name]
+    probs = _shape_problems()
+    pre = [i % 3 for i in range(len(probs))]
+    nsteps = 4
+    alone = []
+    for p, k in zip(probs, pre):
+        with mhd.Solver.from_problem(p, prec=mhd.FP32) as s:
+            s.step(k + 2 * nsteps, sync=True)
+            alone.append(s.read())
+    solvers = [mhd.Solver.from_problem(p, prec=mhd.FP32) for p in probs]
+    for s, k in zip(solvers, pre):
+        if k:
+            s.step(k, sync=True)
+    with mhd.Batch(solvers) as b:
+        b.configure(threads_per_cta=nt, shapes=_cycle(shapes, len(probs)))
+        b.step(nsteps)
+        b.step(nsteps)
+        assert b.sync() == mhd.MHD_OK
+    for s, ref, k, p in zip(solvers, alone, pre, probs):
+        assert s.state()[2] == k + 2 * nsteps
+        assert np.array_equal(s.read(), ref), p.name
+        s.close()
+
+
+def test_batch_configure_rejects_bad_values(mhd):
+    s = mhd.Solver.from_problem(I.random_smooth((8, 8, 8), seed=5), prec=mhd.FP32)
+    with mhd.Batch([s]) as b:
+        for kw in ({"threads_per_cta": 64}, {"ctas_per_sm": -1}, {"spin_cycles": -1},
+                   {"shapes": [{"march_len": 100}]}, {"shapes": [{"seg_k": 4}]},
+                   {"shapes": [{"ct_march": 2}]}, {"shapes": [{"alone": 3}]},
+                   {"shapes": [{"z_warps": -2}]}):
+            with pytest.raises(mhd.MhdError):
+                b.configure(**kw)
+        b.configure(threads_per_cta=256, shapes=[{"march_len": 256}])
+        b.step(2)
+        assert b.sync() == mhd.MHD_OK
+    s.close()
+
+
+def test_batch_timeout_marks_contexts(mhd):
+    """A persistent launch whose waits give up (a bound of one SM cycle: the first item
+    that finds its operation's predecessor unfinished gives up) reports MHD_ERR_TIMEOUT, and
+    every context of the launch reports it from then on, until it is initialised again."""
+    probs = [I.batched_instance(i, lo=24, hi=48) for i in range(4)]
+    solvers = [mhd.Solver.from_problem(p, prec=mhd.FP32) for p in probs]
+    with mhd.Batch(solvers) as b:
+        b.configure(spin_cycles=1)
+        b.step(2)
+        assert b.sync() == mhd.MHD_ERR_TIMEOUT
+        for s in solvers:
+            with pytest.raises(mhd.MhdError) as ei:
+                s.read()
+            assert ei.value.status == mhd.MHD_ERR_TIMEOUT
+        b.configure()                         # the default bound again
+        for s, p in zip(solvers, probs):
+            s.init_fields(p.fields)
+        b.step(2)
+        assert b.sync() == mhd.MHD_OK
+    for s, p in zip(solvers, probs):
+        with mhd.Solver.from_problem(p, prec=mhd.FP32) as r:
+            r.step(2, sync=True)
+            assert np.array_equal(s.read(), r.read())
+        s.close()
