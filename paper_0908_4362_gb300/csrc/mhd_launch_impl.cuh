@@ -112,14 +112,20 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
   if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
     constexpr int K = 2, SEG = 32 * K - 6;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
-    fluid_seg_z<T, LAST, PM, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
-                                              32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
+    const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
+    if (seg_off32<T>(g))
+      fluid_seg_z<T, LAST, PM, kSegWarps, K, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
+    else
+      fluid_seg_z<T, LAST, PM, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
     return;
   }
   constexpr int K = SegK<T>::K, SEG = 32 * K - 6;
   const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
-  fluid_seg_z<T, LAST, PM, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps),
-                                            32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
+  const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
+  if (seg_off32<T>(g))
+    fluid_seg_z<T, LAST, PM, kSegWarps, K, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
+  else
+    fluid_seg_z<T, LAST, PM, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
 }
 
 template <typename T>
@@ -185,17 +191,36 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
   if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
     constexpr int K = 2, SEG = 32 * K - 8;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
-    ct_seg_z<T, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps), 32 * kSegWarps, 0,
-                                s>>>(g, in, out, h, ds);
+    const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
+    if (seg_off32<T>(g))
+      ct_seg_z<T, kSegWarps, K, 1, false, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+    else
+      ct_seg_z<T, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
     return cudaGetLastError();
   }
   {
     constexpr int K = SegK<T>::K, SEG = 32 * K - 8;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
-    ct_seg_z<T, kSegWarps, K><<<(unsigned)((warps + kSegWarps - 1) / kSegWarps), 32 * kSegWarps, 0,
-                                s>>>(g, in, out, h, ds);
+    const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
+    if (seg_off32<T>(g))
+      ct_seg_z<T, kSegWarps, K, 1, false, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+    else
+      ct_seg_z<T, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
     return cudaGetLastError();
   }
+}
+
+// the two-pass z segments: outflow z re-clamps its ghost cells between the passes
+template <typename T, int K>
+static cudaError_t ct2_seg_z_launch(const GridDesc& g, const FieldSet<T>& in,
+                                    const FieldSet<T>& out, double h, DevScalars* ds,
+                                    unsigned nb, bool clamp, cudaStream_t s) {
+  const bool o32 = seg_off32<T>(g);
+  if (clamp && o32) ct_seg_z<T, kSegWarps, K, 2, true, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+  else if (clamp) ct_seg_z<T, kSegWarps, K, 2, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+  else if (o32) ct_seg_z<T, kSegWarps, K, 2, false, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+  else ct_seg_z<T, kSegWarps, K, 2, false><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -218,16 +243,12 @@ static cudaError_t ct2_impl(const GridDesc& g, const FieldSet<T>& in, const Fiel
     constexpr int K = 2, SEG = 32 * K - 16;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
     const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
-    if (clamp) ct_seg_z<T, kSegWarps, K, 2, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
-    else ct_seg_z<T, kSegWarps, K, 2, false><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
-    return cudaGetLastError();
+    return ct2_seg_z_launch<T, K>(g, in, out, h, ds, nb, clamp, s);
   }
   constexpr int K = SegK<T>::K, SEG = 32 * K - 16;
   const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
   const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
-  if (clamp) ct_seg_z<T, kSegWarps, K, 2, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
-  else ct_seg_z<T, kSegWarps, K, 2, false><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
-  return cudaGetLastError();
+  return ct2_seg_z_launch<T, K>(g, in, out, h, ds, nb, clamp, s);
 }
 
 template <typename T>

@@ -57,6 +57,36 @@ __device__ __forceinline__ T ldx(const T* p) {
   else return *p;
 }
 
+// Element addressing of the z segments: a 64-bit element index, or (OFF32, for fields of
+// less than 4 GiB each) an unsigned 32-bit byte offset from the field's base pointer, so
+// that an access adds a 32-bit offset to a kernel-parameter base instead of doing 64-bit
+// index arithmetic per field.  Offsets of neighbours below may be negative: unsigned
+// arithmetic modulo 2^32 still yields the right in-range offset.
+template <typename T, bool OFF32> struct SegAddr {
+  using I = long long;
+  static __device__ __forceinline__ I of(long long e) { return e; }
+  static __device__ __forceinline__ const T* at(const T* p, I i) { return p + i; }
+  static __device__ __forceinline__ T* at(T* p, I i) { return p + i; }
+};
+template <typename T> struct SegAddr<T, true> {
+  using I = unsigned;
+  static __device__ __forceinline__ I of(long long e) { return (unsigned)(e * (long long)sizeof(T)); }
+  static __device__ __forceinline__ const T* at(const T* p, I i) {
+    return reinterpret_cast<const T*>(reinterpret_cast<const char*>(p) + i);
+  }
+  static __device__ __forceinline__ T* at(T* p, I i) {
+    return reinterpret_cast<T*>(reinterpret_cast<char*>(p) + i);
+  }
+};
+#ifndef MHD_OFF32
+#define MHD_OFF32 1
+#endif
+// the 32-bit byte offsets fit: every field of the grid spans less than 4 GiB
+template <typename T>
+__host__ __device__ inline bool seg_off32(const GridDesc& g) {
+  return MHD_OFF32 && (unsigned long long)g.n[0] * g.n[1] * g.n[2] * sizeof(T) <= 0xFFFFFFFFull;
+}
+
 template <typename T>
 __device__ __forceinline__ T shdown(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 template <typename T>
@@ -143,10 +173,11 @@ __device__ __forceinline__ void seg_stage2(const V (&fr2)[K], const V (&fl2)[K],
 }
 
 // one warp: window `wid` (seg_place); all 32 lanes call it
-template <typename T, bool LAST, int PM, int K, bool NC>
+template <typename T, bool LAST, int PM, int K, bool NC, bool OFF32 = false>
 __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                                  const FieldSet<T>& out, T gamma, double h,
                                                  DevScalars* ds, long long wid) {
+  using AD = SegAddr<T, OFF32>;
   constexpr int H = 3, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
@@ -155,24 +186,28 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
   const bool warp_active = sp.active;
   const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
   const T hd = T(0.5) * dth;
-  const long long row = (long long)x * g.s[0] + (long long)y * g.s[1];
-  const long long r1 = row + (long long)(wrap_index(x + 1, g.n[0], g.bc[0]) - x) * g.s[0];
-  const long long r2 = row + (long long)(wrap_index(y + 1, g.n[1], g.bc[1]) - y) * g.s[1];
+  const typename AD::I row = AD::of((long long)x * g.s[0] + (long long)y * g.s[1]);
+  const typename AD::I r1 =
+      row + AD::of((long long)(wrap_index(x + 1, g.n[0], g.bc[0]) - x) * g.s[0]);
+  const typename AD::I r2 =
+      row + AD::of((long long)(wrap_index(y + 1, g.n[1], g.bc[1]) - y) * g.s[1]);
   const int z0 = s0 - H + lane * K;     // the lane's first cell
   // local coordinates of a z sweep: n = z, t1 = x, t2 = y
   T u[K][5], b[K][3];
   int st = 0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    const int zc = wrap_index(z0 + i, nz, bcz), zn = wrap_index(z0 + i + 1, nz, bcz);
-    u[i][0] = ldx<NC>(in.f[0] + row + zc);
-    u[i][1] = ldx<NC>(in.f[3] + row + zc);
-    u[i][2] = ldx<NC>(in.f[1] + row + zc);
-    u[i][3] = ldx<NC>(in.f[2] + row + zc);
-    u[i][4] = ldx<NC>(in.f[4] + row + zc);
-    b[i][0] = T(0.5) * (ldx<NC>(in.f[7] + row + zc) + ldx<NC>(in.f[7] + row + zn));
-    b[i][1] = T(0.5) * (ldx<NC>(in.f[5] + row + zc) + ldx<NC>(in.f[5] + r1 + zc));
-    b[i][2] = T(0.5) * (ldx<NC>(in.f[6] + row + zc) + ldx<NC>(in.f[6] + r2 + zc));
+    const typename AD::I zc = AD::of(wrap_index(z0 + i, nz, bcz));
+    const typename AD::I zn = AD::of(wrap_index(z0 + i + 1, nz, bcz));
+    const typename AD::I c = row + zc;
+    u[i][0] = ldx<NC>(AD::at(in.f[0], c));
+    u[i][1] = ldx<NC>(AD::at(in.f[3], c));
+    u[i][2] = ldx<NC>(AD::at(in.f[1], c));
+    u[i][3] = ldx<NC>(AD::at(in.f[2], c));
+    u[i][4] = ldx<NC>(AD::at(in.f[4], c));
+    b[i][0] = T(0.5) * (ldx<NC>(AD::at(in.f[7], c)) + ldx<NC>(AD::at(in.f[7], row + zn)));
+    b[i][1] = T(0.5) * (ldx<NC>(AD::at(in.f[5], c)) + ldx<NC>(AD::at(in.f[5], r1 + zc)));
+    b[i][2] = T(0.5) * (ldx<NC>(AD::at(in.f[6], c)) + ldx<NC>(AD::at(in.f[6], r2 + zc)));
   }
   // stage 1: first-order fluxes, half step
   T uh[K][5];
@@ -228,12 +263,12 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
   for (int i = 0; i < K; ++i) {
     const int w = lane * K + i, z = z0 + i;
     if (warp_active && w >= H && w < H + SEG && z < nz) {
-      const long long co = row + z;
-      out.f[0][co] = un[i][0];
-      out.f[3][co] = un[i][1];
-      out.f[1][co] = un[i][2];
-      out.f[2][co] = un[i][3];
-      out.f[4][co] = un[i][4];
+      const typename AD::I co = row + AD::of(z);
+      *AD::at(out.f[0], co) = un[i][0];
+      *AD::at(out.f[3], co) = un[i][1];
+      *AD::at(out.f[1], co) = un[i][2];
+      *AD::at(out.f[2], co) = un[i][3];
+      *AD::at(out.f[4], co) = un[i][4];
       if (!(un[i][0] > T(0))) st |= ST_UNPHYSICAL;
       if (LAST) {
         const T v = cell_cmax<T, PM>(un[i][0], un[i][1], un[i][2], un[i][3], un[i][4], b[i][0],
@@ -260,11 +295,11 @@ template <typename T> struct SegMinBlocks {
   static constexpr int fluid = sizeof(T) == 4 ? MHD_SEG_MINB : 0;
   static constexpr int ct = sizeof(T) == 4 ? MHD_CTSEG_MINB : 0;
 };
-template <typename T, bool LAST, int PM, int NW, int K>
+template <typename T, bool LAST, int PM, int NW, int K, bool OFF32 = false>
 __global__ void __launch_bounds__(32 * NW, SegMinBlocks<T>::fluid)
 fluid_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, DevScalars* ds) {
-  fluid_seg_z_warp<T, LAST, PM, K, true>(g, in, out, gamma, h, ds,
-                                          (long long)blockIdx.x * NW + (threadIdx.x >> 5));
+  fluid_seg_z_warp<T, LAST, PM, K, true, OFF32>(g, in, out, gamma, h, ds,
+                                                 (long long)blockIdx.x * NW + (threadIdx.x >> 5));
 }
 
 // one EMF pipeline over the window: bt[] becomes the advected B_t (valid on window cells
@@ -390,10 +425,11 @@ __device__ __forceinline__ void reclamp_window(V (&x)[K], int zw0, int z0, int n
 // advect exactly what the neighbouring pencils' own pipelines advect) and adds its EMF
 // differences to the first pass's B_z.  Every cell runs the operations of two single passes
 // in the same order, so the result is the same bits; the halo doubles (8 cells per side).
-template <typename T, int K, bool NC, int PASSES = 1, bool CLAMPZ = false>
+template <typename T, int K, bool NC, int PASSES = 1, bool CLAMPZ = false, bool OFF32 = false>
 __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                               const FieldSet<T>& out, double h, DevScalars* ds,
                                               long long wid) {
+  using AD = SegAddr<T, OFF32>;
   constexpr int H = 4 * PASSES, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
@@ -402,9 +438,11 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
   const bool warp_active = sp.active;
   const T dth = (T)(ds->dt / h);
   const T hd = T(0.5) * dth;
-  const long long row = (long long)x * g.s[0] + (long long)y * g.s[1];
+  const typename AD::I row = AD::of((long long)x * g.s[0] + (long long)y * g.s[1]);
   const TransverseOffsets o1 = transverse_offsets(x, g.n[0], g.bc[0], g.s[0]);
   const TransverseOffsets o2 = transverse_offsets(y, g.n[1], g.bc[1], g.s[1]);
+  const typename AD::I l1 = AD::of(o1.lo), h1 = AD::of(o1.hi), l2 = AD::of(o2.lo),
+                       h2 = AD::of(o2.hi);
   const int z0 = s0 - H + lane * K;
   const T* pr = in.f[0];
   const T* pm = in.f[3];
@@ -413,18 +451,19 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
   T vo1[K], vn1[K], vo2[K], vn2[K], b1o[K], b1h[K], b2o[K], b2h[K], ba[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    const long long c = row + wrap_index(z0 + i, nz, bcz);
+    const typename AD::I c = row + AD::of(wrap_index(z0 + i, nz, bcz));
+    const typename AD::I cl1 = c + l1, ch1 = c + h1, cl2 = c + l2, ch2 = c + h2;
     T r[5], m[5];
-    r[0] = ldx<NC>(pr + c);           m[0] = ldx<NC>(pm + c);
-    r[1] = ldx<NC>(pr + c + o1.lo);   m[1] = ldx<NC>(pm + c + o1.lo);
-    r[2] = ldx<NC>(pr + c + o1.hi);   m[2] = ldx<NC>(pm + c + o1.hi);
-    r[3] = ldx<NC>(pr + c + o2.lo);   m[3] = ldx<NC>(pm + c + o2.lo);
-    r[4] = ldx<NC>(pr + c + o2.hi);   m[4] = ldx<NC>(pm + c + o2.hi);
-    b1o[i] = ldx<NC>(in.f[5] + c);
-    b1h[i] = ldx<NC>(in.f[5] + c + o1.hi);
-    b2o[i] = ldx<NC>(in.f[6] + c);
-    b2h[i] = ldx<NC>(in.f[6] + c + o2.hi);
-    ba[i] = ldx<NC>(in.f[7] + c);
+    r[0] = ldx<NC>(AD::at(pr, c));     m[0] = ldx<NC>(AD::at(pm, c));
+    r[1] = ldx<NC>(AD::at(pr, cl1));   m[1] = ldx<NC>(AD::at(pm, cl1));
+    r[2] = ldx<NC>(AD::at(pr, ch1));   m[2] = ldx<NC>(AD::at(pm, ch1));
+    r[3] = ldx<NC>(AD::at(pr, cl2));   m[3] = ldx<NC>(AD::at(pm, cl2));
+    r[4] = ldx<NC>(AD::at(pr, ch2));   m[4] = ldx<NC>(AD::at(pm, ch2));
+    b1o[i] = ldx<NC>(AD::at(in.f[5], c));
+    b1h[i] = ldx<NC>(AD::at(in.f[5], ch1));
+    b2o[i] = ldx<NC>(AD::at(in.f[6], c));
+    b2h[i] = ldx<NC>(AD::at(in.f[6], ch2));
+    ba[i] = ldx<NC>(AD::at(in.f[7], c));
     vo1[i] = Num<T>::div(m[0] + m[1], r[0] + r[1]);
     vn1[i] = o1.hi_across_lo ? Num<T>::div(m[2] + m[1], r[2] + r[1])
                              : Num<T>::div(m[2] + m[0], r[2] + r[0]);
@@ -495,10 +534,10 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
   for (int i = 0; i < K; ++i) {
     const int w = lane * K + i, z = z0 + i;
     if (warp_active && w >= H && w < H + SEG && z < nz) {
-      const long long co = row + z;
-      out.f[5][co] = b1o[i];
-      out.f[6][co] = b2o[i];
-      out.f[7][co] = bA[i];
+      const typename AD::I co = row + AD::of(z);
+      *AD::at(out.f[5], co) = b1o[i];
+      *AD::at(out.f[6], co) = b2o[i];
+      *AD::at(out.f[7], co) = bA[i];
       if (!(b1o[i] == b1o[i]) || !(b2o[i] == b2o[i]) || !(bA[i] == bA[i])) st |= ST_NONFINITE;
     }
   }
@@ -506,11 +545,11 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
 }
 
 // CLAMPZ: the z axis is outflow (the two-pass form re-clamps its ghost cells between passes)
-template <typename T, int NW, int K, int PASSES = 1, bool CLAMPZ = false>
+template <typename T, int NW, int K, int PASSES = 1, bool CLAMPZ = false, bool OFF32 = false>
 __global__ void __launch_bounds__(32 * NW, SegMinBlocks<T>::ct)
 ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
-  ct_seg_z_warp<T, K, true, PASSES, CLAMPZ>(g, in, out, h, ds,
-                                            (long long)blockIdx.x * NW + (threadIdx.x >> 5));
+  ct_seg_z_warp<T, K, true, PASSES, CLAMPZ, OFF32>(g, in, out, h, ds,
+                                                   (long long)blockIdx.x * NW + (threadIdx.x >> 5));
 }
 
 }  // namespace mhd
