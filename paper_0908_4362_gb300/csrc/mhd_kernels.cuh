@@ -109,6 +109,41 @@ __device__ __forceinline__ T ffms(T s, T a, T b) {
   else return b - s * a;
 }
 
+// Element addressing of a field: a 64-bit element index, or (OFF32, for fields of less
+// than 4 GiB each) an unsigned 32-bit byte offset from the field's base pointer, so
+// that an access adds a 32-bit offset to a kernel-parameter base instead of doing 64-bit
+// index arithmetic per field.  Offsets of neighbours below may be negative: unsigned
+// arithmetic modulo 2^32 still yields the right in-range offset.
+template <typename T, bool OFF32> struct FieldAddr {
+  using I = long long;
+  static __device__ __forceinline__ I of(long long e) { return e; }
+  static __device__ __forceinline__ const T* at(const T* p, I i) { return p + i; }
+  static __device__ __forceinline__ T* at(T* p, I i) { return p + i; }
+};
+template <typename T> struct FieldAddr<T, true> {
+  using I = unsigned;
+  static __device__ __forceinline__ I of(long long e) { return (unsigned)(e * (long long)sizeof(T)); }
+  static __device__ __forceinline__ const T* at(const T* p, I i) {
+    return reinterpret_cast<const T*>(reinterpret_cast<const char*>(p) + i);
+  }
+  static __device__ __forceinline__ T* at(T* p, I i) {
+    return reinterpret_cast<T*>(reinterpret_cast<char*>(p) + i);
+  }
+};
+#ifndef MHD_OFF32
+#define MHD_OFF32 1
+#endif
+// the 32-bit byte offsets fit: every field of the grid spans less than 4 GiB
+template <typename T>
+__host__ __device__ inline bool field_off32(const GridDesc& g) {
+  return MHD_OFF32 && (unsigned long long)g.n[0] * g.n[1] * g.n[2] * sizeof(T) <= 0xFFFFFFFFull;
+}
+// the x/y fluid march stores by 32-bit offsets too (measured: fluid x/y -3.5% at 512^3;
+// the shared-row CT's stores were 1-2.5% slower that way and keep 64-bit indices)
+#ifndef MHD_OFF32_XY
+#define MHD_OFF32_XY 1
+#endif
+
 __device__ __forceinline__ int wrap_index(int i, int n, int bc) {
   if (i >= 0 && i < n) return i;
   if (bc == 0) {

@@ -32,6 +32,9 @@ static cudaError_t set_march_attr() {
         fluid_march_xy_vec<A, LAST, PM, MarchCfg<T>::S, MarchCfg<T>::NT>,
         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
     if (e2 != cudaSuccess) e = e2;
+    e2 = cudaFuncSetAttribute(fluid_march_xy_vec<A, LAST, PM, MarchCfg<T>::S, MarchCfg<T>::NT, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_tile_smem<T>());
+    if (e2 != cudaSuccess) e = e2;
     e2 = cudaFuncSetAttribute(fluid_march_xy_tma<A, LAST, PM, MarchCfg<T>::S>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_march_smem());
     if (e2 != cudaSuccess) e = e2;
@@ -100,8 +103,15 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
         return;
       }
       if (march_vec<T>(g)) {
-        if (axis == 0) fluid_march_xy_vec<0, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
-        else fluid_march_xy_vec<1, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        const bool o32 = MHD_OFF32_XY && field_off32<T>(g);
+        if (axis == 0 && o32)
+          fluid_march_xy_vec<0, LAST, PM, S, NT, true><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        else if (axis == 0)
+          fluid_march_xy_vec<0, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        else if (o32)
+          fluid_march_xy_vec<1, LAST, PM, S, NT, true><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
+        else
+          fluid_march_xy_vec<1, LAST, PM, S, NT><<<grid, NT, sm, s>>>(g, in, out, gamma, h, ds);
         return;
       }
     }
@@ -113,7 +123,7 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
     constexpr int K = 2, SEG = 32 * K - 6;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
     const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
-    if (seg_off32<T>(g))
+    if (field_off32<T>(g))
       fluid_seg_z<T, LAST, PM, kSegWarps, K, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
     else
       fluid_seg_z<T, LAST, PM, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
@@ -122,7 +132,7 @@ static void fluid_dispatch(const GridDesc& g, const FieldSet<T>& in, const Field
   constexpr int K = SegK<T>::K, SEG = 32 * K - 6;
   const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
   const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
-  if (seg_off32<T>(g))
+  if (field_off32<T>(g))
     fluid_seg_z<T, LAST, PM, kSegWarps, K, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
   else
     fluid_seg_z<T, LAST, PM, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, gamma, h, ds);
@@ -192,7 +202,7 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
     constexpr int K = 2, SEG = 32 * K - 8;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
     const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
-    if (seg_off32<T>(g))
+    if (field_off32<T>(g))
       ct_seg_z<T, kSegWarps, K, 1, false, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
     else
       ct_seg_z<T, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
@@ -202,7 +212,7 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
     constexpr int K = SegK<T>::K, SEG = 32 * K - 8;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
     const unsigned nb = (unsigned)((warps + kSegWarps - 1) / kSegWarps);
-    if (seg_off32<T>(g))
+    if (field_off32<T>(g))
       ct_seg_z<T, kSegWarps, K, 1, false, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
     else
       ct_seg_z<T, kSegWarps, K><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
@@ -215,7 +225,7 @@ template <typename T, int K>
 static cudaError_t ct2_seg_z_launch(const GridDesc& g, const FieldSet<T>& in,
                                     const FieldSet<T>& out, double h, DevScalars* ds,
                                     unsigned nb, bool clamp, cudaStream_t s) {
-  const bool o32 = seg_off32<T>(g);
+  const bool o32 = field_off32<T>(g);
   if (clamp && o32) ct_seg_z<T, kSegWarps, K, 2, true, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
   else if (clamp) ct_seg_z<T, kSegWarps, K, 2, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);
   else if (o32) ct_seg_z<T, kSegWarps, K, 2, false, true><<<nb, 32 * kSegWarps, 0, s>>>(g, in, out, h, ds);

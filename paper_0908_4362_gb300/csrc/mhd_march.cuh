@@ -297,11 +297,12 @@ __device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
 #endif
 }
 
-template <int A, bool LAST, int PM, int S, int NT>
+template <int A, bool LAST, int PM, int S, int NT, bool OFF32 = false>
 __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const FieldSet<float>& in,
                                                         const FieldSet<float>& out, float gamma,
                                                         double h, DevScalars* ds, unsigned bx,
                                                         unsigned by, unsigned char* smem_raw) {
+  using AD = FieldAddr<float, OFF32>;
   static_assert(A == 0 || A == 1, "x or y sweep");
   static_assert(NT % 32 == 0, "whole warps");
   using T = float;
@@ -385,12 +386,12 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
     if (P.push(k, u0, b0, gamma, dth, hd, un, bo)) {
       const int ia = j - 3;
       if (active) {
-        const long long co = base + (long long)ia * sA;
-        out.f[0][co] = un[0];
-        out.f[1 + A][co] = un[1];
-        out.f[1 + T1][co] = un[2];
-        out.f[1 + T2][co] = un[3];
-        out.f[4][co] = un[4];
+        const typename AD::I co = AD::of(base + (long long)ia * sA);
+        *AD::at(out.f[0], co) = un[0];
+        *AD::at(out.f[1 + A], co) = un[1];
+        *AD::at(out.f[1 + T1], co) = un[2];
+        *AD::at(out.f[1 + T2], co) = un[3];
+        *AD::at(out.f[4], co) = un[4];
         if (!(un[0] > T(0))) P.st |= ST_UNPHYSICAL;
         if (LAST) {
           const T v = cell_cmax<T, PM>(un[0], un[1], un[2], un[3], un[4], bo[0], bo[1], bo[2],
@@ -443,13 +444,13 @@ fluid_march_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, T gamma, double h, D
 #ifndef MHD_VEC_MINB
 #define MHD_VEC_MINB 4
 #endif
-template <int A, bool LAST, int PM, int S, int NT>
+template <int A, bool LAST, int PM, int S, int NT, bool OFF32 = false>
 __global__ void __launch_bounds__(NT, MHD_VEC_MINB)
 fluid_march_xy_vec(GridDesc g, FieldSet<float> in, FieldSet<float> out, float gamma, double h,
                    DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fluid_march_xy_tile_vec<A, LAST, PM, S, NT>(g, in, out, gamma, h, ds, blockIdx.x, blockIdx.y,
-                                               smem_raw);
+  fluid_march_xy_tile_vec<A, LAST, PM, S, NT, OFF32>(g, in, out, gamma, h, ds, blockIdx.x,
+                                                      blockIdx.y, smem_raw);
 }
 
 }  // namespace mhd

@@ -57,36 +57,6 @@ __device__ __forceinline__ T ldx(const T* p) {
   else return *p;
 }
 
-// Element addressing of the z segments: a 64-bit element index, or (OFF32, for fields of
-// less than 4 GiB each) an unsigned 32-bit byte offset from the field's base pointer, so
-// that an access adds a 32-bit offset to a kernel-parameter base instead of doing 64-bit
-// index arithmetic per field.  Offsets of neighbours below may be negative: unsigned
-// arithmetic modulo 2^32 still yields the right in-range offset.
-template <typename T, bool OFF32> struct SegAddr {
-  using I = long long;
-  static __device__ __forceinline__ I of(long long e) { return e; }
-  static __device__ __forceinline__ const T* at(const T* p, I i) { return p + i; }
-  static __device__ __forceinline__ T* at(T* p, I i) { return p + i; }
-};
-template <typename T> struct SegAddr<T, true> {
-  using I = unsigned;
-  static __device__ __forceinline__ I of(long long e) { return (unsigned)(e * (long long)sizeof(T)); }
-  static __device__ __forceinline__ const T* at(const T* p, I i) {
-    return reinterpret_cast<const T*>(reinterpret_cast<const char*>(p) + i);
-  }
-  static __device__ __forceinline__ T* at(T* p, I i) {
-    return reinterpret_cast<T*>(reinterpret_cast<char*>(p) + i);
-  }
-};
-#ifndef MHD_OFF32
-#define MHD_OFF32 1
-#endif
-// the 32-bit byte offsets fit: every field of the grid spans less than 4 GiB
-template <typename T>
-__host__ __device__ inline bool seg_off32(const GridDesc& g) {
-  return MHD_OFF32 && (unsigned long long)g.n[0] * g.n[1] * g.n[2] * sizeof(T) <= 0xFFFFFFFFull;
-}
-
 template <typename T>
 __device__ __forceinline__ T shdown(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 template <typename T>
@@ -177,7 +147,7 @@ template <typename T, bool LAST, int PM, int K, bool NC, bool OFF32 = false>
 __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                                  const FieldSet<T>& out, T gamma, double h,
                                                  DevScalars* ds, long long wid) {
-  using AD = SegAddr<T, OFF32>;
+  using AD = FieldAddr<T, OFF32>;
   constexpr int H = 3, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
@@ -429,7 +399,7 @@ template <typename T, int K, bool NC, int PASSES = 1, bool CLAMPZ = false, bool 
 __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
                                               const FieldSet<T>& out, double h, DevScalars* ds,
                                               long long wid) {
-  using AD = SegAddr<T, OFF32>;
+  using AD = FieldAddr<T, OFF32>;
   constexpr int H = 4 * PASSES, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
