@@ -341,17 +341,25 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
   float* ring = reinterpret_cast<float*>(smem_raw) + (size_t)w * kMarchRing * RS;
   const int js = a0 - 3;
   const int kend = min(S, nA - a0) + 6;
+  // offsets of the next row to stage (an) and of the row after it (B_A, one cell ahead):
+  // rows advance by sA and take the wrap of the axis only where they cross its ends
+  int an = js;
+  long long offc = (long long)wrap_index(an, nA, bcA) * sA;
+  long long offn = (long long)wrap_index(an + 1, nA, bcA) * sA;
   auto issue = [&](int kk) {
     if (kk < kend) {
-      const long long off = (long long)wrap_index(js + kk, nA, bcA) * sA;
       float* slot = ring + (size_t)(kk % kMarchRing) * RS + 4 * q;
       if (gq) {
-        const long long off1 = r == 1 ? (long long)wrap_index(js + kk + 1, nA, bcA) * sA : off;
-        cp_async_16(slot + r * 32, src0 + off);
+        const long long off1 = r == 1 ? offn : offc;
+        cp_async_16(slot + r * 32, src0 + offc);
         cp_async_16(slot + (4 + r) * 32, src1 + off1);
-        if (lane < 8) cp_async_16(slot + 8 * 32, src2 + off);
+        if (lane < 8) cp_async_16(slot + 8 * 32, src2 + offc);
       }
-      if (special) cp_async_elem(ring + (size_t)(kk % kMarchRing) * RS + 9 * 32 + lane, srcs + off);
+      if (special) cp_async_elem(ring + (size_t)(kk % kMarchRing) * RS + 9 * 32 + lane, srcs + offc);
+      offc = offn;
+      ++an;
+      if ((unsigned)an < (unsigned)(nA - 1)) offn += sA;   // an and an + 1 inside the axis
+      else offn = (long long)wrap_index(an + 1, nA, bcA) * sA;
     }
     cp_async_commit();
   };
