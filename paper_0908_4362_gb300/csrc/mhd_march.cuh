@@ -104,6 +104,22 @@ __device__ __forceinline__ long long wrap_off(int i, int n, int bc, long long st
   return (long long)wrap_index(i, n, bc) * stride;
 }
 
+// Offset of the next row along the sweep axis that a march stages: rows advance by the
+// axis stride, and take the axis' wrap only where they cross its ends (one compare per row
+// instead of a wrap and a 64-bit product; the index arithmetic is a large share of the
+// issue-bound marches)
+struct RowCursor {
+  int a, n, bc;
+  long long s, off;
+  __device__ __forceinline__ RowCursor(int a0, int n_, int bc_, long long s_)
+      : a(a0), n(n_), bc(bc_), s(s_), off((long long)wrap_index(a0, n_, bc_) * s_) {}
+  __device__ __forceinline__ void advance() {
+    if ((unsigned)a < (unsigned)(n - 1)) off += s;      // a and a + 1 inside the axis
+    else off = (long long)wrap_index(a + 1, n, bc) * s;
+    ++a;
+  }
+};
+
 // Asynchronous global -> shared copies (cp.async): each thread prefetches the inputs of
 // the iterations D ahead of the one it computes into its own slots of a shared ring, so
 // that the loads of a march stay in flight while the arithmetic of earlier cells runs.
@@ -208,11 +224,13 @@ __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, cons
   // shared ring: [slot][value][thread], 10 values per iteration (u, B_n(j+1), B_t1 x2, B_t2 x2)
   T* ring = reinterpret_cast<T*>(smem_raw);
   constexpr int NV = 10;
+  RowCursor rc(js, nA, bcA, sA), rn(js + 1, nA, bcA, sA);
   auto issue = [&](int kk) {
     if (kk < kend) {
-      const int j = js + kk;
-      const long long c = base + wrap_off<T>(j, nA, bcA, sA);
-      const long long cn = base + wrap_off<T>(j + 1, nA, bcA, sA);
+      const long long c = base + rc.off;
+      const long long cn = base + rn.off;
+      rc.advance();
+      rn.advance();
       T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
       cp_async_elem(slot + 0 * NT, pr + c);
       cp_async_elem(slot + 1 * NT, pn + c);
@@ -688,9 +706,11 @@ __device__ __forceinline__ void ct_march_xy_tile(const GridDesc& g, const FieldS
   const int kend = min(S, nA - a0) + 8;
   T* ring = reinterpret_cast<T*>(smem_raw);
   constexpr int NV = 15;
+  RowCursor rc(js, nA, bcA, sA);
   auto issue = [&](int kk) {
     if (kk < kend) {
-      const long long c = base + (long long)wrap_index(js + kk, nA, bcA) * sA;
+      const long long c = base + rc.off;
+      rc.advance();
       T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
       cp_async_elem(slot + 0 * NT, pr + c);
       cp_async_elem(slot + 1 * NT, pr + c + o1.lo);
@@ -933,9 +953,11 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
       src[q] = f + (long long)orow_c * g.s[O] + zb + 4 * grp;
       dst[q] = row * VW + 4 * grp;
     }
+    RowCursor rc(js, nA, bcA, sA);
     auto issue = [&](int kk) {
       if (kk < kend) {
-        const long long off = (long long)wrap_index(js + kk, nA, bcA) * sA;
+        const long long off = rc.off;
+        rc.advance();
         float* slot = wring + (size_t)(kk % kMarchRing) * VR * VW;
 #pragma unroll
         for (int q = 0; q < 2; ++q)
@@ -958,9 +980,11 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
     }
   } else {
     constexpr int NV = 9;
+    RowCursor rc(js, nA, bcA, sA);
     auto issue = [&](int kk) {
       if (kk < kend) {
-        const long long c = base + (long long)wrap_index(js + kk, nA, bcA) * sA;
+        const long long c = base + rc.off;
+        rc.advance();
         T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
         cp_async_elem(slot + 0 * NT, pr + c);
         cp_async_elem(slot + 1 * NT, pr + c + lo1);
@@ -994,9 +1018,15 @@ static size_t ct_rows_smem(int R, int passes = 1) {
   return sizeof(T) * ((size_t)kMarchRing * 9 * 32 * R + 2 * (size_t)passes * 32 * R);
 }
 
-// the two-pass form asks for 2 resident blocks (at most 128 registers a thread)
+// resident blocks per SM asked of the compiler: 2 for the two-pass form (at most 128
+// registers a thread), MHD_ROWS1_MINB for the FP32 one-pass form (0: none; the compiler
+// takes 88 registers, 2 blocks of 256 threads per SM; a cap at 3 blocks, 79 registers, was
+// 5% slower at 512^3)
+#ifndef MHD_ROWS1_MINB
+#define MHD_ROWS1_MINB 0
+#endif
 template <typename T, int A, int S, int R, int PASSES = 1>
-__global__ void __launch_bounds__(32 * R, PASSES == 2 ? 2 : 0)
+__global__ void __launch_bounds__(32 * R, PASSES == 2 ? 2 : (sizeof(T) == 4 ? MHD_ROWS1_MINB : 0))
 ct_rows_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ct_rows_xy_tile<T, A, S, R, PASSES>(g, in, out, h, ds, blockIdx.x, blockIdx.y, smem_raw);
