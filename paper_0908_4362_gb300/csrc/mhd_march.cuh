@@ -645,10 +645,14 @@ struct CtColumn {
   __device__ __forceinline__ void push(const T r[5], const T m[5], T b1o, T b1h, T b2o, T b2h,
                                        T ba, bool hx1, bool hx2, T dth, T hd, T* bt1, T* bt2,
                                        T* bA) {
+    // the upper row's face velocity: across its lower face, the own cell, or (outflow upper
+    // edge) the lower neighbour; the operands are chosen first, one quotient each
+    const T mx1 = hx1 ? m[1] : m[0], rx1 = hx1 ? r[1] : r[0];
+    const T mx2 = hx2 ? m[3] : m[0], rx2 = hx2 ? r[3] : r[0];
     const T vo1 = Num<T>::div(m[0] + m[1], r[0] + r[1]);
-    const T vn1 = hx1 ? Num<T>::div(m[2] + m[1], r[2] + r[1]) : Num<T>::div(m[2] + m[0], r[2] + r[0]);
+    const T vn1 = Num<T>::div(m[2] + mx1, r[2] + rx1);
     const T vo2 = Num<T>::div(m[0] + m[3], r[0] + r[3]);
-    const T vn2 = hx2 ? Num<T>::div(m[4] + m[3], r[4] + r[3]) : Num<T>::div(m[4] + m[0], r[4] + r[0]);
+    const T vn2 = Num<T>::div(m[4] + mx2, r[4] + rx2);
     T eo1, en1, eo2, en2;
     if constexpr (PACK) {
       const float2 ndth = splat2(-(float)dth * kEmf2Inv), nhd = splat2(-(float)hd * kEmf2Inv);

@@ -434,12 +434,14 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
     b2o[i] = ldx<NC>(AD::at(in.f[6], c));
     b2h[i] = ldx<NC>(AD::at(in.f[6], ch2));
     ba[i] = ldx<NC>(AD::at(in.f[7], c));
+    // the upper row's face velocity: across its lower face, the own cell, or (outflow
+    // upper edge) the lower neighbour; the operands are chosen first, one quotient each
+    const T mx1 = o1.hi_across_lo ? m[1] : m[0], rx1 = o1.hi_across_lo ? r[1] : r[0];
+    const T mx2 = o2.hi_across_lo ? m[3] : m[0], rx2 = o2.hi_across_lo ? r[3] : r[0];
     vo1[i] = Num<T>::div(m[0] + m[1], r[0] + r[1]);
-    vn1[i] = o1.hi_across_lo ? Num<T>::div(m[2] + m[1], r[2] + r[1])
-                             : Num<T>::div(m[2] + m[0], r[2] + r[0]);
+    vn1[i] = Num<T>::div(m[2] + mx1, r[2] + rx1);
     vo2[i] = Num<T>::div(m[0] + m[3], r[0] + r[3]);
-    vn2[i] = o2.hi_across_lo ? Num<T>::div(m[4] + m[3], r[4] + r[3])
-                             : Num<T>::div(m[4] + m[0], r[4] + r[0]);
+    vn2[i] = Num<T>::div(m[4] + mx2, r[4] + rx2);
   }
   T eo1[K], en1[K], eo2[K], en2[K];
   constexpr bool PACK = sizeof(T) == 4 && MHD_CT_PACK;
