@@ -231,7 +231,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, cons
       const long long cn = base + rn.off;
       rc.advance();
       rn.advance();
-      T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
+      T* slot = ring + (size_t)((unsigned)kk % kMarchRing) * NV * NT + threadIdx.x;
       cp_async_elem(slot + 0 * NT, pr + c);
       cp_async_elem(slot + 1 * NT, pn + c);
       cp_async_elem(slot + 2 * NT, p1 + c);
@@ -255,7 +255,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, cons
   for (int k = 0; k < kend; ++k) {
     issue(k + kMarchDepth);
     cp_async_wait<kMarchDepth>();
-    const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+    const T* slot = ring + (size_t)((unsigned)k % kMarchRing) * NV * NT + threadIdx.x;
     const int j = js + k;
     T u0[5], b0[3];
 #pragma unroll
@@ -366,14 +366,14 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
   long long offn = (long long)wrap_index(an + 1, nA, bcA) * sA;
   auto issue = [&](int kk) {
     if (kk < kend) {
-      float* slot = ring + (size_t)(kk % kMarchRing) * RS + 4 * q;
+      float* slot = ring + (size_t)((unsigned)kk % kMarchRing) * RS + 4 * q;
       if (gq) {
         const long long off1 = r == 1 ? offn : offc;
         cp_async_16(slot + r * 32, src0 + offc);
         cp_async_16(slot + (4 + r) * 32, src1 + off1);
         if (lane < 8) cp_async_16(slot + 8 * 32, src2 + offc);
       }
-      if (special) cp_async_elem(ring + (size_t)(kk % kMarchRing) * RS + 9 * 32 + lane, srcs + offc);
+      if (special) cp_async_elem(ring + (size_t)((unsigned)kk % kMarchRing) * RS + 9 * 32 + lane, srcs + offc);
       offc = offn;
       ++an;
       if ((unsigned)an < (unsigned)(nA - 1)) offn += sA;   // an and an + 1 inside the axis
@@ -391,13 +391,16 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
   bool nan_seen = false;
   constexpr int ZROW = (A == 0) ? 7 : 6;     // the row holding B_z (B_t2 for x, B_t1 for y)
   const int nb_idx = special ? 9 * 32 + lane : ZROW * 32 + lane + 1;
+  // output offset of iteration k (cell j - 3 = a0 - 6 + k; used from k = 6 on, inside the
+  // tile), advanced by one row per iteration
+  typename AD::I co = AD::of(base + (long long)(a0 - 6) * sA);
+  const typename AD::I dco = AD::of(sA);
 #pragma unroll kFluidUnroll
-  for (int k = 0; k < kend; ++k) {
+  for (int k = 0; k < kend; ++k, co += dco) {
     cp_async_wait<kMarchDepth - 1>();
     __syncwarp();
     issue(k + kMarchDepth);
-    const float* slot = ring + (size_t)(k % kMarchRing) * RS;
-    const int j = js + k;
+    const float* slot = ring + (size_t)((unsigned)k % kMarchRing) * RS;
     T u0[5], b0[3];
 #pragma unroll
     for (int c = 0; c < 5; ++c) u0[c] = slot[c * 32 + lane];
@@ -410,9 +413,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
     bn_cur = bn_next;
     T un[5], bo[3];
     if (P.push(k, u0, b0, gamma, dth, hd, un, bo)) {
-      const int ia = j - 3;
       if (active) {
-        const typename AD::I co = AD::of(base + (long long)ia * sA);
         *AD::at(out.f[0], co) = un[0];
         *AD::at(out.f[1 + A], co) = un[1];
         *AD::at(out.f[1 + T1], co) = un[2];
@@ -715,7 +716,7 @@ __device__ __forceinline__ void ct_march_xy_tile(const GridDesc& g, const FieldS
     if (kk < kend) {
       const long long c = base + rc.off;
       rc.advance();
-      T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
+      T* slot = ring + (size_t)((unsigned)kk % kMarchRing) * NV * NT + threadIdx.x;
       cp_async_elem(slot + 0 * NT, pr + c);
       cp_async_elem(slot + 1 * NT, pr + c + o1.lo);
       cp_async_elem(slot + 2 * NT, pr + c + o1.hi);
@@ -741,7 +742,7 @@ __device__ __forceinline__ void ct_march_xy_tile(const GridDesc& g, const FieldS
   for (int k = 0; k < kend; ++k) {
     issue(k + kMarchDepth);
     cp_async_wait<kMarchDepth>();
-    const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+    const T* slot = ring + (size_t)((unsigned)k % kMarchRing) * NV * NT + threadIdx.x;
     const int j = js + k;
     T r[5], m[5];
 #pragma unroll
@@ -962,7 +963,7 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
       if (kk < kend) {
         const long long off = rc.off;
         rc.advance();
-        float* slot = wring + (size_t)(kk % kMarchRing) * VR * VW;
+        float* slot = wring + (size_t)((unsigned)kk % kMarchRing) * VR * VW;
 #pragma unroll
         for (int q = 0; q < 2; ++q)
           if (has[q]) cp_async_16(slot + dst[q], src[q] + off);
@@ -978,7 +979,7 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
       cp_async_wait<kMarchDepth - 1>();
       __syncwarp();
       issue(k + kMarchDepth);
-      const float* sl = wring + (size_t)(k % kMarchRing) * VR * VW;
+      const float* sl = wring + (size_t)((unsigned)k % kMarchRing) * VR * VW;
       cell(k, (T)sl[own], (T)sl[l1], (T)sl[l2], (T)sl[VW + own], (T)sl[VW + l1],
            (T)sl[VW + l2], (T)sl[4 * VW + own], (T)sl[5 * VW + own], (T)sl[6 * VW + own]);
     }
@@ -989,7 +990,7 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
       if (kk < kend) {
         const long long c = base + rc.off;
         rc.advance();
-        T* slot = ring + (size_t)(kk % kMarchRing) * NV * NT + threadIdx.x;
+        T* slot = ring + (size_t)((unsigned)kk % kMarchRing) * NV * NT + threadIdx.x;
         cp_async_elem(slot + 0 * NT, pr + c);
         cp_async_elem(slot + 1 * NT, pr + c + lo1);
         cp_async_elem(slot + 2 * NT, pr + c + lo2);
@@ -1008,7 +1009,7 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
     for (int k = 0; k < kend; ++k) {
       issue(k + kMarchDepth);
       cp_async_wait<kMarchDepth>();
-      const T* slot = ring + (size_t)(k % kMarchRing) * NV * NT + threadIdx.x;
+      const T* slot = ring + (size_t)((unsigned)k % kMarchRing) * NV * NT + threadIdx.x;
       cell(k, slot[0], slot[1 * NT], slot[2 * NT], slot[3 * NT], slot[4 * NT], slot[5 * NT],
            slot[6 * NT], slot[7 * NT], slot[8 * NT]);
     }
