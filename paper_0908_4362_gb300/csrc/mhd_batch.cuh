@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NT, MHD_BATCH_MINB * 128 / NT) batch_kernel(Ba
     const BatchInst& ins = a.inst[it.inst];
     const int warp = threadIdx.x >> 5;
     if (op.kind == OP_DT) {
-      if (threadIdx.x == 0) dt_update<float>(ins.ds, ins.cfl_h);
+      if (threadIdx.x == 0) dt_update<float>(ins.ds, ins.cfl_h, ins.h);
     } else if (op.kind == OP_CMAX || op.kind == OP_CTFLAT) {
       constexpr int kFlat = NT * kFlatPerThread;
       const long long N = (long long)op.g.n[0] * op.g.n[1] * op.g.n[2];
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(NT, MHD_BATCH_MINB * 128 / NT) batch_kernel(Ba
       if (op.kind == OP_CMAX) {
         cmax_range<float, PM_FP32>(op.g, op.in, ins.gamma, ins.ds, i0 + threadIdx.x, i1, NT);
       } else {
-        const float dth = (float)(ins.ds->dt / ins.h);
+        const float dth = step_factor<float>(ins.ds, ins.h);
         int st;
         if (op.axis == 0)
           st = ct_flat_range<float, 0>(op.g, op.in, op.out, dth, i0 + threadIdx.x, i1, NT);

@@ -153,7 +153,7 @@ static cudaError_t enqueue_step_t(mhd_ctx* ctx, int phase) {
   cudaError_t e;
   {
     ProfScope ps(ctx, 6);
-    e = Launch<T>::dt(ctx->ds, ctx->cfg.cfl * ctx->cfg.h, ctx->stream);
+    e = Launch<T>::dt(ctx->ds, ctx->cfg.cfl * ctx->cfg.h, ctx->cfg.h, ctx->stream);
   }
   if (e != cudaSuccess) return e;
   const int* o = kOrder[phase];
@@ -547,6 +547,9 @@ mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt) {
   mhd_status s = sync_scalars(ctx);
   if (s != MHD_OK) return s;
   CK(cudaMemcpyAsync(&ctx->ds->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "dt");
+  const float dt_h = (float)(dt / ctx->cfg.h);    // as dt_update stores it
+  CK(cudaMemcpyAsync(&ctx->ds->dt_h, &dt_h, sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+     "dt/h");
   cudaError_t e;
   if (ctx->esz == 4)
     e = op == 0 ? enqueue_fluid<float>(ctx, axis, false)

@@ -75,7 +75,7 @@ template <typename T, int A>
 __global__ void ct_flat_kernel(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h,
                                DevScalars* ds) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-  const T dth = (T)(ds->dt / h);
+  const T dth = step_factor<T>(ds, h);
   const int st = ct_flat_range<T, A>(g, in, out, dth,
                                      blockIdx.x * (long long)blockDim.x + threadIdx.x, N,
                                      (long long)gridDim.x * blockDim.x);

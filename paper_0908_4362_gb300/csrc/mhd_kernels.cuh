@@ -42,6 +42,8 @@ struct DevScalars {
   unsigned long long cmax;   // bits of the c_max of the current state (float or double)
   int steps_done;            // steps that advanced t
   int status;                // sticky ST_* bits
+  float dt_h;                // (float)(dt / h): the step factor of the FP32 sweeps
+  int pad_;
   // partial maxima of the running c_max: warps fold their maximum into one of these slots
   // (atomicMax), spreading what would be one contended address over kCmaxSlots; dt_update
   // and the host fold them into cmax
@@ -430,7 +432,7 @@ __global__ void cmax_kernel(GridDesc g, FieldSet<T> in, T gamma, DevScalars* ds)
 
 // dt = cfl h / c_max on the device, clipped to land on t_end (Sect. 4.2 steps 4-5, 8-9)
 template <typename T>
-__device__ __forceinline__ void dt_update(DevScalars* ds, double cfl_h) {
+__device__ __forceinline__ void dt_update(DevScalars* ds, double cfl_h, double h) {
   const double cm = Num<T>::from_bits(fold_cmax_bits(*ds));
   double dt = cfl_h / cm;
   int clipped = 0, active = 1;
@@ -449,6 +451,7 @@ __device__ __forceinline__ void dt_update(DevScalars* ds, double cfl_h) {
     }
   }
   ds->dt = dt;
+  ds->dt_h = (float)(dt / h);
   if (active) {
     ds->t = clipped ? ds->t_end : ds->t + 2.0 * dt;
     ds->dt_last = dt;
@@ -459,8 +462,18 @@ __device__ __forceinline__ void dt_update(DevScalars* ds, double cfl_h) {
 }
 
 template <typename T>
-__global__ void dt_kernel(DevScalars* ds, double cfl_h) {
-  dt_update<T>(ds, cfl_h);
+__global__ void dt_kernel(DevScalars* ds, double cfl_h, double h) {
+  dt_update<T>(ds, cfl_h, h);
+}
+
+// dt/h of the step in flight in the sweep's precision.  FP32 sweeps read the factor that
+// dt_update (or mhd_apply) stored, (float)(dt / h), the same rounded value, instead of each
+// thread dividing in FP64, which runs at GB300's low FP64 rate (and the z segments would do
+// it once per 3 cells)
+template <typename T>
+__device__ __forceinline__ T step_factor(const DevScalars* ds, double h) {
+  if constexpr (sizeof(T) == 4) return ds->dt_h;
+  else return ds->dt / h;
 }
 
 // Exact float -> double by re-biasing the bits of normal numbers (and zeros) with integer

@@ -30,7 +30,7 @@ struct Launch {
                          double h, DevScalars* ds, int axis, cudaStream_t s);
   static cudaError_t cmax(const GridDesc& g, const FieldSet<T>& in, double gamma,
                           DevScalars* ds, int pm, cudaStream_t s);
-  static cudaError_t dt(DevScalars* ds, double cfl_h, cudaStream_t s);
+  static cudaError_t dt(DevScalars* ds, double cfl_h, double h, cudaStream_t s);
   static cudaError_t sums(long long n, const FieldSet<T>& in, double* partial, int nblocks,
                           double* out, cudaStream_t s);
   // dst (T) <- src (dtype 0 float, 1 double), device pointers

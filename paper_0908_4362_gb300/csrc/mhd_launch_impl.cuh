@@ -315,8 +315,9 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
       double gamma, DevScalars* ds, int pm, cudaStream_t s) {                             \
     return cmax_impl<T>(g, in, gamma, ds, pm, s);                                          \
   }                                                                                         \
-  template <> cudaError_t Launch<T>::dt(DevScalars* ds, double cfl_h, cudaStream_t s) {     \
-    dt_kernel<T><<<1, 1, 0, s>>>(ds, cfl_h);                                                \
+  template <> cudaError_t Launch<T>::dt(DevScalars* ds, double cfl_h, double h,           \
+                                        cudaStream_t s) {                                   \
+    dt_kernel<T><<<1, 1, 0, s>>>(ds, cfl_h, h);                                             \
     return cudaGetLastError();                                                              \
   }                                                                                         \
   template <> cudaError_t Launch<T>::sums(long long n, const FieldSet<T>& in,               \

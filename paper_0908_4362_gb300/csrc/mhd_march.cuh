@@ -198,7 +198,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_elem(const GridDesc& g, cons
   const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
   const bool active = o_ < g.n[O];
-  const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
+  const T dth = step_factor<T>(ds, h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
   const T hd = T(0.5) * dth;
   const int zc = min(z, g.n[2] - 1), oc = min(o, g.n[O] - 1);
   const long long base = (long long)zc + (long long)oc * g.s[O];
@@ -335,7 +335,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_vec(const GridDesc& g, const
   const int o = active ? (int)(p / nz) : nO - 1;
   const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
-  const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);
+  const T dth = step_factor<T>(ds, h) * T(FluxScale<T>::inv);
   const T hd = T(0.5) * dth;
   const long long sA = g.s[A], sO = g.s[O];
   // this lane's copies: group q of rows r and r + 4 (and of row 8 for lanes 0-7)
@@ -693,7 +693,7 @@ __device__ __forceinline__ void ct_march_xy_tile(const GridDesc& g, const FieldS
   const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
   const bool active = o_ < g.n[O];
-  const T dth = (T)(ds->dt / h);
+  const T dth = (T)(ds->dt / h);   // step_factor's value; a division once per tile here
   const T hd = T(0.5) * dth;
   const long long base = (long long)z + (long long)oc * g.s[O];
   const int c1 = (T1 == 2) ? z : oc, c2 = (T2 == 2) ? z : oc;
@@ -826,7 +826,7 @@ __device__ __forceinline__ void ct_rows_xy_tile(const GridDesc& g, const FieldSe
   const bool halo_row = (w == R - 1);        // supplies the O-row EMF only
   const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
-  const T dth = (T)(ds->dt / h);
+  const T dth = (T)(ds->dt / h);   // step_factor's value; a division once per tile here
   const T hd = T(0.5) * dth;
   const long long base = (long long)zc + (long long)oc * g.s[O];
   const int oc_lo = wrap_index(oc - 1, g.n[O], g.bc[O]);

@@ -154,7 +154,7 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
   const SegPlace sp = seg_place(g, nz, SEG, wid);
   const int s0 = sp.s0, x = sp.x, y = sp.y;
   const bool warp_active = sp.active;
-  const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
+  const T dth = step_factor<T>(ds, h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
   const T hd = T(0.5) * dth;
   const typename AD::I row = AD::of((long long)x * g.s[0] + (long long)y * g.s[1]);
   const typename AD::I r1 =
@@ -406,7 +406,7 @@ __device__ __forceinline__ void ct_seg_z_warp(const GridDesc& g, const FieldSet<
   const SegPlace sp = seg_place(g, nz, SEG, wid);
   const int s0 = sp.s0, x = sp.x, y = sp.y;
   const bool warp_active = sp.active;
-  const T dth = (T)(ds->dt / h);
+  const T dth = step_factor<T>(ds, h);
   const T hd = T(0.5) * dth;
   const typename AD::I row = AD::of((long long)x * g.s[0] + (long long)y * g.s[1]);
   const TransverseOffsets o1 = transverse_offsets(x, g.n[0], g.bc[0], g.s[0]);

@@ -136,7 +136,7 @@ __device__ __forceinline__ void fluid_march_xy_tile_tma(const GridDesc& g, const
   const int oup = wrap_index(o + 1, nO, g.bc[O]);
   const int a0 = by * S;
   const int nA = g.n[A], bcA = g.bc[A];
-  const T dth = (T)(ds->dt / h) * T(FluxScale<T>::inv);
+  const T dth = step_factor<T>(ds, h) * T(FluxScale<T>::inv);
   const T hd = T(0.5) * dth;
   const long long sA = g.s[A], sO = g.s[O];
   // the ring on a 128-byte boundary of the shared window (box destinations)
