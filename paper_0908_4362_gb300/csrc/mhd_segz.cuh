@@ -36,16 +36,28 @@ struct SegPlace {
   int s0, x, y;
   bool active;
 };
+template <bool DIV32 = false>
 __device__ __forceinline__ SegPlace seg_place(const GridDesc& g, int nz, int seg, long long wid) {
   const int nseg = (nz + seg - 1) / seg;
   const long long total = (long long)g.n[0] * g.n[1] * nseg;
   SegPlace p;
   p.active = wid < total;
   const long long w = p.active ? wid : total - 1;
-  const long long pencil = w / nseg;
-  p.s0 = (int)(w % nseg) * seg;
-  p.x = (int)(pencil / g.n[1]);
-  p.y = (int)(pencil % g.n[1]);
+  if (DIV32 && total <= 0xFFFFFFFFll) {
+    // 32-bit unsigned divisions: every lane computes its warp's window, and a 64-bit
+    // division per lane and window was a measurable share of the fluid segments (-1.3%;
+    // the CT segments, at a 56-register cap, were 6.7% slower this way and keep 64 bits)
+    const unsigned w32 = (unsigned)w, ns = (unsigned)nseg, n1 = (unsigned)g.n[1];
+    const unsigned pencil = w32 / ns;
+    p.s0 = (int)(w32 - pencil * ns) * seg;
+    p.x = (int)(pencil / n1);
+    p.y = (int)(pencil - (unsigned)p.x * n1);
+  } else {
+    const long long pencil = w / nseg;
+    p.s0 = (int)(w % nseg) * seg;
+    p.x = (int)(pencil / g.n[1]);
+    p.y = (int)(pencil % g.n[1]);
+  }
   return p;
 }
 
@@ -151,7 +163,7 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
   constexpr int H = 3, SEG = 32 * K - 2 * H;
   const int lane = threadIdx.x & 31;
   const int nz = g.n[2], bcz = g.bc[2];
-  const SegPlace sp = seg_place(g, nz, SEG, wid);
+  const SegPlace sp = seg_place<true>(g, nz, SEG, wid);
   const int s0 = sp.s0, x = sp.x, y = sp.y;
   const bool warp_active = sp.active;
   const T dth = step_factor<T>(ds, h) * T(FluxScale<T>::inv);   // for cell_flux's flux scale
