@@ -1023,15 +1023,15 @@ static size_t ct_rows_smem(int R, int passes = 1) {
   return sizeof(T) * ((size_t)kMarchRing * 9 * 32 * R + 2 * (size_t)passes * 32 * R);
 }
 
-// resident blocks per SM asked of the compiler: 2 for the two-pass form (at most 128
-// registers a thread), MHD_ROWS1_MINB for the FP32 one-pass form (0: none; the compiler
+// resident blocks per SM asked of the compiler: for the two-pass form 2 (at most 128
+// registers a thread) or, with 16 rows (512 threads), 1; MHD_ROWS1_MINB for the FP32 one-pass form (0: none; the compiler
 // takes 88 registers, 2 blocks of 256 threads per SM; a cap at 3 blocks, 79 registers, was
 // 5% slower at 512^3)
 #ifndef MHD_ROWS1_MINB
 #define MHD_ROWS1_MINB 0
 #endif
 template <typename T, int A, int S, int R, int PASSES = 1>
-__global__ void __launch_bounds__(32 * R, PASSES == 2 ? 2 : (sizeof(T) == 4 ? MHD_ROWS1_MINB : 0))
+__global__ void __launch_bounds__(32 * R, PASSES == 2 ? (R >= 16 ? 1 : 2) : (sizeof(T) == 4 ? MHD_ROWS1_MINB : 0))
 ct_rows_xy(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ct_rows_xy_tile<T, A, S, R, PASSES>(g, in, out, h, ds, blockIdx.x, blockIdx.y, smem_raw);
