@@ -52,15 +52,17 @@ static cudaError_t set_ct_march_attr() {
 #ifndef MHD_ROWS_R
 #define MHD_ROWS_R 16
 #endif
-constexpr int kRowsR = MHD_ROWS_R;
+// (FP64 keeps 8 rows: its pipelines need 160 registers, which 512 threads cannot have)
+template <typename T> struct RowsCfg { static constexpr int R = sizeof(T) == 4 ? MHD_ROWS_R : 8; };
 template <typename T, int A>
 static cudaError_t set_ct_rows_attr() {
-  cudaError_t e = cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, kRowsR>,
+  constexpr int R = RowsCfg<T>::R;
+  cudaError_t e = cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)ct_rows_smem<T>(kRowsR));
-  const cudaError_t e2 = cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, kRowsR, 2>,
+                                       (int)ct_rows_smem<T>(R));
+  const cudaError_t e2 = cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, R, 2>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)ct_rows_smem<T>(kRowsR, 2));
+                                              (int)ct_rows_smem<T>(R, 2));
   return e != cudaSuccess ? e : e2;
 }
 
@@ -182,7 +184,7 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
     return cudaGetLastError();
   }
   if (ct_use_rows(g, axis)) {
-    constexpr int R = kRowsR;
+    constexpr int R = RowsCfg<T>::R;
     const int o = axis == 0 ? 1 : 0;
     const long long nb = (long long)((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1));
     const dim3 grid((unsigned)nb, (unsigned)((g.n[axis] + S - 1) / S));
@@ -241,7 +243,7 @@ static cudaError_t ct2_impl(const GridDesc& g, const FieldSet<T>& in, const Fiel
   if (axis_is_flat(g, axis)) return cudaErrorNotSupported;
   if (axis < 2) {
     if (!ct_use_rows(g, axis) || g.bc[axis] != 0) return cudaErrorNotSupported;
-    constexpr int S = MarchCfg<T>::S, R = kRowsR;
+    constexpr int S = MarchCfg<T>::S, R = RowsCfg<T>::R;
     const int o = axis == 0 ? 1 : 0;
     const long long nb = (long long)((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1));
     const dim3 grid((unsigned)nb, (unsigned)((g.n[axis] + S - 1) / S));
