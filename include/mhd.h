@@ -281,10 +281,10 @@ mhd_status mhd_vis_range(mhd_ctx* ctx, int quantity, double* vmin, double* vmax)
  * Returns MHD_ERR_INVALID for a NULL argument, a bad dtype, n < 1, or
  * n > MHD_SUMS_NOALLOC_MAX_CELLS (the scratch holds one row of partial sums per 65,536
  * cells, 4096 rows); MHD_ERR_CUDA if a CUDA call fails.  The first call on a device looks
- * up the scratch array's device address with that device current; make that first call
- * before any stream capture.  The address is kept for the life of the process: a
- * cudaDeviceReset of that device makes it stale.  All calls share the one scratch array:
- * calls whose work overlaps on the GPU race, so serialise them. */
+ * up the scratch array's device address with that device current.  The address is kept
+ * for the life of the process: a cudaDeviceReset of that device makes it stale.  All calls
+ * share the one scratch array: calls whose work overlaps on the GPU race, so serialise
+ * them. */
 #define MHD_SUMS_NOALLOC_MAX_CELLS 268435456LL
 mhd_status mhd_sums_noalloc(const void* const f[8], int dtype, long long n, double out[8],
                             void* stream);

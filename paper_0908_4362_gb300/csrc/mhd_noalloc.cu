@@ -9,10 +9,9 @@
 // the library image: every GPU that loads the library holds it until the process exits.
 //
 // The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current) and remembers it; that first call must
-// come before any stream capture.  Every call shares the one array: calls whose work
-// overlaps on the GPU race on it, so the caller serialises them (one stream, or
-// synchronise between calls).  Each call writes every scratch slot it later reads, so
+// cudaGetSymbolAddress (with that device current) and remembers it.  Every call shares the
+// one array: calls whose work overlaps on the GPU race on it, so the caller serialises them
+// (one stream, or synchronise between calls).  Each call writes every scratch slot it later reads, so
 // nothing left by an earlier call needs clearing.
 #include <mutex>
 
