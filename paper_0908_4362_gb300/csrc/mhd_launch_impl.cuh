@@ -46,17 +46,17 @@ static cudaError_t set_ct_march_attr() {
   return cudaFuncSetAttribute(ct_march_xy<T, A, MarchCfg<T>::S, MarchCfg<T>::NT>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem<T>(15));
 }
-// CT with shared EMF rows (ct_rows_xy): warps per block (used where ct_use_rows).  16 rows
-// (one block of 512 threads per SM, 15 updated rows each) measured 2% faster than 8 at
-// 512^3 and 4 rows 16% slower
+// CT with shared EMF rows (ct_rows_xy): warps per block (used where ct_use_rows).  FP32
+// launches with at least kRowsWideMin blocks of 16 rows per SM take 16 rows (one block of 512
+// threads per SM, 15 updated rows each: 2% faster than 8 at 512^3), smaller ones 8 (16 rows
+// left a 256^3 launch at about 2 waves and ran 14% slower); 4 rows were 16% slower at 512^3.
+// FP64 always takes 8: its pipelines need 160 registers, which 512 threads cannot have.
 #ifndef MHD_ROWS_R
 #define MHD_ROWS_R 16
 #endif
-// (FP64 keeps 8 rows: its pipelines need 160 registers, which 512 threads cannot have)
-template <typename T> struct RowsCfg { static constexpr int R = sizeof(T) == 4 ? MHD_ROWS_R : 8; };
-template <typename T, int A>
-static cudaError_t set_ct_rows_attr() {
-  constexpr int R = RowsCfg<T>::R;
+constexpr int kRowsWide = MHD_ROWS_R, kRowsNarrow = 8, kRowsWideMin = 8;
+template <typename T, int A, int R>
+static cudaError_t set_ct_rows_attr_r() {
   cudaError_t e = cudaFuncSetAttribute(ct_rows_xy<T, A, MarchCfg<T>::S, R>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)ct_rows_smem<T>(R));
@@ -64,6 +64,50 @@ static cudaError_t set_ct_rows_attr() {
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)ct_rows_smem<T>(R, 2));
   return e != cudaSuccess ? e : e2;
+}
+template <typename T, int A>
+static cudaError_t set_ct_rows_attr() {
+  cudaError_t e = set_ct_rows_attr_r<T, A, kRowsNarrow>();
+  if constexpr (sizeof(T) == 4 && kRowsWide != kRowsNarrow) {
+    const cudaError_t e2 = set_ct_rows_attr_r<T, A, kRowsWide>();
+    if (e2 != cudaSuccess) e = e2;
+  }
+  return e;
+}
+// the shared-row CT along axis (0 or 1) with R warps a block, PASSES operator applications
+template <typename T, int R, int PASSES>
+static cudaError_t launch_ct_rows_r(const GridDesc& g, const FieldSet<T>& in,
+                                    const FieldSet<T>& out, double h, DevScalars* ds, int axis,
+                                    cudaStream_t s) {
+  constexpr int S = MarchCfg<T>::S;
+  const int o = axis == 0 ? 1 : 0;
+  const long long nb = (long long)((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1));
+  const dim3 grid((unsigned)nb, (unsigned)((g.n[axis] + S - 1) / S));
+  const size_t sm = ct_rows_smem<T>(R, PASSES);
+  if (axis == 0) ct_rows_xy<T, 0, S, R, PASSES><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
+  else ct_rows_xy<T, 1, S, R, PASSES><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
+  return cudaGetLastError();
+}
+template <typename T, int PASSES>
+static cudaError_t launch_ct_rows(const GridDesc& g, const FieldSet<T>& in,
+                                  const FieldSet<T>& out, double h, DevScalars* ds, int axis,
+                                  cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && kRowsWide != kRowsNarrow) {
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 152;
+    }
+    const int o = axis == 0 ? 1 : 0;
+    const long long wide = (long long)((g.n[2] + 30) / 31) *
+                           ((g.n[o] + kRowsWide - 2) / (kRowsWide - 1)) *
+                           ((g.n[axis] + MarchCfg<T>::S - 1) / MarchCfg<T>::S);
+    if (wide >= (long long)kRowsWideMin * sms)
+      return launch_ct_rows_r<T, kRowsWide, PASSES>(g, in, out, h, ds, axis, s);
+  }
+  return launch_ct_rows_r<T, kRowsNarrow, PASSES>(g, in, out, h, ds, axis, s);
 }
 
 template <typename T, int PM>
@@ -183,16 +227,7 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
     else ct_flat_kernel<T, 2><<<(unsigned)nb, 256, 0, s>>>(g, in, out, h, ds);
     return cudaGetLastError();
   }
-  if (ct_use_rows(g, axis)) {
-    constexpr int R = RowsCfg<T>::R;
-    const int o = axis == 0 ? 1 : 0;
-    const long long nb = (long long)((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1));
-    const dim3 grid((unsigned)nb, (unsigned)((g.n[axis] + S - 1) / S));
-    const size_t sm = ct_rows_smem<T>(R);
-    if (axis == 0) ct_rows_xy<T, 0, S, R><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
-    else ct_rows_xy<T, 1, S, R><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
-    return cudaGetLastError();
-  }
+  if (ct_use_rows(g, axis)) return launch_ct_rows<T, 1>(g, in, out, h, ds, axis, s);
   if (axis == 0 || axis == 1) {
     const int o = axis == 0 ? 1 : 0;
     const long long np = (long long)g.n[2] * g.n[o];
@@ -243,14 +278,7 @@ static cudaError_t ct2_impl(const GridDesc& g, const FieldSet<T>& in, const Fiel
   if (axis_is_flat(g, axis)) return cudaErrorNotSupported;
   if (axis < 2) {
     if (!ct_use_rows(g, axis) || g.bc[axis] != 0) return cudaErrorNotSupported;
-    constexpr int S = MarchCfg<T>::S, R = RowsCfg<T>::R;
-    const int o = axis == 0 ? 1 : 0;
-    const long long nb = (long long)((g.n[2] + 30) / 31) * ((g.n[o] + R - 2) / (R - 1));
-    const dim3 grid((unsigned)nb, (unsigned)((g.n[axis] + S - 1) / S));
-    const size_t sm = ct_rows_smem<T>(R, 2);
-    if (axis == 0) ct_rows_xy<T, 0, S, R, 2><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
-    else ct_rows_xy<T, 1, S, R, 2><<<grid, 32 * R, sm, s>>>(g, in, out, h, ds);
-    return cudaGetLastError();
+    return launch_ct_rows<T, 2>(g, in, out, h, ds, axis, s);
   }
   const bool clamp = g.bc[2] == 1;
   if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
