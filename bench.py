@@ -45,13 +45,13 @@ STEP_ALG_BYTES = 384
 # DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
 # a step) from ncu captures on a 256^3 grid (the ncu summaries under profiles/), keyed by the
 # hash of the kernel sources they were taken on; another hash reports null.
-NCU_TRAFFIC_PER_CELL = {"1ff5b81da064503e": 50.73}
+NCU_TRAFFIC_PER_CELL = {"6493be2955de5ac4": 50.74}
 # thread instructions per cell of one launch of each sweep kernel (ncu
 # smsp__thread_inst_executed.sum / cells, 256^3; one launch in six of each axis's fluid sweeps
 # also reduces c_max and is weighted in), keyed like the traffic: the sweeps are bound by
 # instruction issue, and this gives the issue rate they reach beside the HBM roofline
-NCU_INSTR_PER_CELL = {"1ff5b81da064503e": {"fluid_x": 313.7, "fluid_y": 313.7, "fluid_z": 388.0,
-                                           "ct_x": 178.4, "ct_y": 178.4, "ct_z": 283.7}}
+NCU_INSTR_PER_CELL = {"6493be2955de5ac4": {"fluid_x": 313.3, "fluid_y": 313.3, "fluid_z": 364.9,
+                                           "ct_x": 178.4, "ct_y": 178.4, "ct_z": 263.8}}
 
 
 KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.cuh",
