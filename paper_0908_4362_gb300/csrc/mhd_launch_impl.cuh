@@ -1,6 +1,8 @@
 // Launcher bodies shared by the per-precision translation units.
 #pragma once
 
+#include <cstdlib>
+
 #include "mhd_flat.cuh"
 #include "mhd_kernels.cuh"
 #include "mhd_launch.h"
@@ -214,6 +216,38 @@ static cudaError_t fluid_impl(const GridDesc& g, const FieldSet<T>& in, const Fi
   return cudaGetLastError();
 }
 
+// FP32 constrained transport along z by the marching shared-row kernel (ct_rows_z), one or
+// two passes; false where its grid does not fit, or where the environment variable
+// MHD_CTZ_SEG is "1" (read at each launch: the tests compare both forms bit for bit), and
+// the caller then takes ct_seg_z
+template <int PASSES>
+static bool ct_rows_z_launch(const GridDesc& g, const FieldSet<float>& in,
+                             const FieldSet<float>& out, double h, DevScalars* ds,
+                             cudaStream_t s) {
+  if (!MHD_CTZ_ROWS) return false;
+  const char* seg = std::getenv("MHD_CTZ_SEG");
+  if (seg && seg[0] == '1') return false;
+  constexpr int Q = MHD_CTZ_Q, L = MHD_CTZ_L;
+  const bool o32 = field_off32<float>(g), clamp = PASSES == 2 && g.bc[2] == 1;
+  dim3 grid;
+  if (seg_k_for(g.n[2]) == 2) {
+    constexpr int K = 2;
+    if (!ct_rows_z_grid<K, PASSES>(g, Q, L, &grid)) return false;
+    if (clamp && o32) ct_rows_z<K, Q, PASSES, true, true><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+    else if (clamp) ct_rows_z<K, Q, PASSES, true, false><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+    else if (o32) ct_rows_z<K, Q, PASSES, false, true><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+    else ct_rows_z<K, Q, PASSES, false, false><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+    return true;
+  }
+  constexpr int K = 3;
+  if (!ct_rows_z_grid<K, PASSES>(g, Q, L, &grid)) return false;
+  if (clamp && o32) ct_rows_z<K, Q, PASSES, true, true><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+  else if (clamp) ct_rows_z<K, Q, PASSES, true, false><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+  else if (o32) ct_rows_z<K, Q, PASSES, false, true><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+  else ct_rows_z<K, Q, PASSES, false, false><<<grid, 32 * Q, 0, s>>>(g, in, out, h, ds, L);
+  return true;
+}
+
 template <typename T>
 static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                            double h, DevScalars* ds, int axis, cudaStream_t s) {
@@ -237,6 +271,8 @@ static cudaError_t ct_impl(const GridDesc& g, const FieldSet<T>& in, const Field
     else ct_march_xy<T, 1, S, NT><<<grid, NT, sm, s>>>(g, in, out, h, ds);
     return cudaGetLastError();
   }
+  if constexpr (sizeof(T) == 4)
+    if (ct_rows_z_launch<1>(g, in, out, h, ds, s)) return cudaGetLastError();
   if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
     constexpr int K = 2, SEG = 32 * K - 8;
     const long long warps = (long long)g.n[0] * g.n[1] * ((g.n[2] + SEG - 1) / SEG);
@@ -280,6 +316,8 @@ static cudaError_t ct2_impl(const GridDesc& g, const FieldSet<T>& in, const Fiel
     if (!ct_use_rows(g, axis) || g.bc[axis] != 0) return cudaErrorNotSupported;
     return launch_ct_rows<T, 2>(g, in, out, h, ds, axis, s);
   }
+  if constexpr (sizeof(T) == 4)
+    if (ct_rows_z_launch<2>(g, in, out, h, ds, s)) return cudaGetLastError();
   const bool clamp = g.bc[2] == 1;
   if (sizeof(T) == 4 && seg_k_for(g.n[2]) == 2) {
     constexpr int K = 2, SEG = 32 * K - 16;

@@ -536,4 +536,194 @@ ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) 
                                                    (long long)blockIdx.x * NW + (threadIdx.x >> 5));
 }
 
+
+// ------------------------------------------------------------------------------------
+// Constrained transport along z with shared EMF rows (FP32): ct_rows_z.
+//
+// ct_seg_z runs four EMF pipelines per pencil: the own row's and the upper row's, for each
+// transverse component; the upper rows' pipelines are the neighbouring pencils' own ones
+// (same operands, the packed lanes independent).  Here a block of Q warps covers Q
+// neighbouring y rows (warp w: pencil y = yb + w) of one z window and marches along x over L
+// rows, and each warp runs only its own pair of pipelines (t1 = x, t2 = y):
+//   - the y-face EMF of the upper y row comes from warp w + 1 through shared memory (double
+//     buffered by row parity, one block barrier per row); warp Q - 1 only supplies it;
+//   - the x-face EMF of the upper x row is the own x-face EMF of the next row of the march,
+//     so the constraint on B_z of row r completes one row later (three values per cell
+//     carried in registers: B_z, the x-face EMF, and the y-face EMF difference);
+//   - the face velocity of the x-face takes rho and m_z of the previous row from registers;
+//     that of the y-face loads the lower y row (the same data warp w - 1 loads: an L1 hit).
+// Per cell: 2 pipelines x Q/(Q-1) x (L+1)/L and 7 loads, against 4 pipelines and 15 loads.
+// At the outflow upper edge of x or y the upper row's pipeline is the own one (the upper row
+// clamps onto the row itself and its face velocity is taken across its lower face), as in
+// ct_seg_z.  Every output value comes from the same operations on the same operands as in
+// ct_seg_z, in the same order, so the two kernels give the same bits; PASSES = 2 is the
+// middle pair of a step (two passes with the same dt, ghost cells re-clamped between passes
+// on an outflow z axis).
+// ------------------------------------------------------------------------------------
+#ifndef MHD_CTZ_ROWS
+#define MHD_CTZ_ROWS 1
+#endif
+#ifndef MHD_CTZ_Q
+#define MHD_CTZ_Q 16
+#endif
+#ifndef MHD_CTZ_L
+#define MHD_CTZ_L 32
+#endif
+// resident blocks asked of the compiler: a 64-register cap (32 / Q blocks of Q warps per SM)
+template <int Q> struct CtRowsZMinBlocks { static constexpr int value = Q <= 32 ? 32 / Q : 1; };
+
+template <int K, int Q, int PASSES = 1, bool CLAMPZ = false, bool OFF32 = false>
+__global__ void __launch_bounds__(32 * Q, CtRowsZMinBlocks<Q>::value)
+ct_rows_z(GridDesc g, FieldSet<float> in, FieldSet<float> out, double h, DevScalars* ds, int L) {
+  using AD = FieldAddr<float, OFF32>;
+  using I = typename AD::I;
+  constexpr int H = 4 * PASSES, W = 32 * K, SEG = W - 2 * H;
+  __shared__ float se[2][PASSES][Q][W];   // y-face EMF of each warp's own pipelines
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int bcx = g.bc[0], bcy = g.bc[1], bcz = g.bc[2];
+  const int yw = (int)blockIdx.x * (Q - 1) + w;          // unwrapped y of the warp's pencil
+  const int s0 = (int)blockIdx.y * SEG;
+  const int xb = (int)blockIdx.z * L;
+  const int xe = min(xb + L, nx);
+  const int y = wrap_index(yw, ny, bcy), ylo = wrap_index(y - 1, ny, bcy);
+  // the upper y row's across-face cell is the lower neighbour: its pipeline is the own one
+  const bool y_edge = wrap_index(wrap_index(y + 1, ny, bcy) - 1, ny, bcy) != y;
+  const bool writer = w < Q - 1 && yw < ny;
+  const int wn = w + 1 < Q ? w + 1 : w;
+  // outflow upper x edge in this block: the last row's upper-row pipeline is its own
+  const bool x_edge = xe == nx && bcx == 1;
+  const float dth = step_factor<float>(ds, h), hd = 0.5f * dth;
+  const float2 ndth2 = splat2(-dth * kEmf2Inv), nhd2 = splat2(-hd * kEmf2Inv);
+  const float dc = dth * kEmf2Inv;                        // the packed EMFs are kEmf2Scale x
+  const int z0 = s0 - H + lane * K;
+  I zc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) zc[i] = AD::of(wrap_index(z0 + i, nz, bcz));
+  const I ys = AD::of((long long)y * g.s[1]), ylos = AD::of((long long)ylo * g.s[1]);
+  // rho and m_z of the row below the first one
+  float rp[K], mp[K];
+  {
+    const I row = AD::of((long long)wrap_index(xb - 1, nx, bcx) * g.s[0]) + ys;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      rp[i] = __ldg(AD::at(in.f[0], row + zc[i]));
+      mp[i] = __ldg(AD::at(in.f[3], row + zc[i]));
+    }
+  }
+  // carried from row r - 1 to row r: B_z, own x-face EMF and y-face EMF difference per pass
+  float bap[K], e1p[PASSES][K], d2p[PASSES][K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    bap[i] = 0.f;
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) e1p[p][i] = d2p[p][i] = 0.f;
+  }
+  I xop = 0;                      // x offset of the previous row
+  int st = 0;
+  // output cells of the window: w in [H, H + SEG), z < nz
+  bool outc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int wc = lane * K + i;
+    outc[i] = writer && wc >= H && wc < H + SEG && z0 + i < nz;
+  }
+  // B_z of the previous row from its carried values and this row's x-face EMF (en1)
+  auto finish_bz = [&](const float (&en1)[PASSES][K]) {
+    float b[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) b[i] = bap[i];
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        b[i] = ffma(dc, en1[p][i] - e1p[p][i], b[i]);   // constraint from t1 = x, then t2 = y
+        b[i] = ffma(dc, d2p[p][i], b[i]);
+      }
+      if (CLAMPZ && p + 1 < PASSES) reclamp_window<float, K>(b, s0 - H, z0, nz);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (outc[i]) {
+        const I co = xop + ys + AD::of(z0 + i);
+        *AD::at(out.f[7], co) = b[i];
+        if (!(b[i] == b[i])) st |= ST_NONFINITE;
+      }
+  };
+  const int rlast = x_edge ? xe - 1 : xe;
+  for (int r = xb; r <= rlast; ++r) {
+    const I xo = AD::of((long long)wrap_index(r, nx, bcx) * g.s[0]);
+    const I row = xo + ys, rowlo = xo + ylos;
+    float r0[K], m0[K], bz[K];
+    float2 vo[K], bo[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const I c = row + zc[i], cl = rowlo + zc[i];
+      r0[i] = __ldg(AD::at(in.f[0], c));
+      m0[i] = __ldg(AD::at(in.f[3], c));
+      const float rl = __ldg(AD::at(in.f[0], cl)), ml = __ldg(AD::at(in.f[3], cl));
+      bo[i] = make_float2(__ldg(AD::at(in.f[5], c)), __ldg(AD::at(in.f[6], c)));
+      bz[i] = __ldg(AD::at(in.f[7], c));
+      vo[i] = make_float2(Num<float>::div(m0[i] + mp[i], r0[i] + rp[i]),
+                          Num<float>::div(m0[i] + ml, r0[i] + rl));
+    }
+    float2 eo[PASSES][K];
+#pragma unroll
+    for (int p = 0; p < PASSES; ++p) {
+      emf_seg2<K>(vo, bo, ndth2, nhd2, eo[p]);
+      if (CLAMPZ && p + 1 < PASSES) reclamp_window<float2, K>(bo, s0 - H, z0, nz);
+    }
+    if (r > xb) {
+      float en1[PASSES][K];
+#pragma unroll
+      for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+        for (int i = 0; i < K; ++i) en1[p][i] = eo[p][i].x;
+      finish_bz(en1);
+    }
+    if (r < xe) {
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (outc[i]) {
+          const I co = row + AD::of(z0 + i);
+          *AD::at(out.f[5], co) = bo[i].x;
+          *AD::at(out.f[6], co) = bo[i].y;
+          if (!(bo[i].x == bo[i].x) || !(bo[i].y == bo[i].y)) st |= ST_NONFINITE;
+        }
+      float(&sw)[PASSES][Q][W] = se[r & 1];
+#pragma unroll
+      for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+        for (int i = 0; i < K; ++i) sw[p][w][lane * K + i] = eo[p][i].y;
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < PASSES; ++p)
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const float en2 = y_edge ? eo[p][i].y : sw[p][wn][lane * K + i];
+          d2p[p][i] = en2 - eo[p][i].y;
+          e1p[p][i] = eo[p][i].x;
+        }
+#pragma unroll
+      for (int i = 0; i < K; ++i) bap[i] = bz[i];
+      xop = xo;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) { rp[i] = r0[i]; mp[i] = m0[i]; }
+  }
+  if (x_edge) finish_bz(e1p);   // the last row's upper-row x-face EMF is its own
+  if (st) atomicOr(&ds->status, st);
+}
+
+// ct_rows_z launch geometry: blocks of Q warps over (y rows, z windows, x row groups)
+template <int K, int PASSES>
+__host__ inline bool ct_rows_z_grid(const GridDesc& g, int Q, int L, dim3* grid) {
+  constexpr int SEG = 32 * K - 8 * PASSES;
+  const long long gx = (g.n[1] + Q - 2) / (Q - 1), gy = (g.n[2] + SEG - 1) / SEG,
+                  gz = (g.n[0] + L - 1) / L;
+  if (gx > 0x7FFFFFFFll || gy > 65535 || gz > 65535) return false;
+  *grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
+  return true;
+}
+
 }  // namespace mhd

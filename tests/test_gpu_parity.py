@@ -423,3 +423,29 @@ def _pair_case(mhd, prob, axis, prec):
     assert np.array_equal(got[0], got[1]), np.abs(got[0] - got[1]).max()
     err = rel_l1(got[1], ref.f)
     assert np.all(err <= (1e-13 if p == mhd.FP64 else 4e-6)), err
+
+
+CTZ_FORM_CASES = ([c for c in OP_CASES if c[0] != "thin"] + [c for c in PAIR_CASES] +
+                  [("rows_blocks_mixed", lambda: I.random_smooth((70, 47, 97), seed=41, bc=(1, 0, 1))),
+                   ("rows_blocks_periodic", lambda: I.random_smooth((64, 31, 180), seed=42))])
+
+
+@pytest.mark.parametrize("case", CTZ_FORM_CASES, ids=[c[0] for c in CTZ_FORM_CASES])
+@pytest.mark.parametrize("op", [1, 2], ids=["ct", "pair"])
+def test_ct_z_rows_same_bits_as_segments(mhd, monkeypatch, case, op):
+    """FP32 CT along z: the marching shared-row kernel (each warp runs its own EMF pipelines,
+    the upper rows' EMFs come from the next row of the march and the neighbouring warp)
+    gives the same bits as the warp segments that run all four pipelines per pencil
+    (MHD_CTZ_SEG=1 selects those), one pass and the middle pair, over periodic, outflow
+    and mixed boundaries, ragged shapes, several row groups along x and y, and windows
+    of 2 and 3 cells per lane."""
+    prob = case[1]()
+    dt = 0.5 * oracle.Oracle.from_problem(prob).dt()
+    got = []
+    for seg in ("1", "0"):
+        monkeypatch.setenv("MHD_CTZ_SEG", seg)
+        with mhd.Solver.from_problem(prob, prec=mhd.FP32) as s:
+            s.apply(op, 2, dt)
+            got.append(s.read())
+    monkeypatch.delenv("MHD_CTZ_SEG")
+    assert np.array_equal(got[0], got[1]), np.abs(got[0] - got[1]).max()
