@@ -95,7 +95,10 @@ mhd_status mhd_step(mhd_ctx* ctx, int nsteps, double t_end, int* steps_done, dou
  * op 1 = CT along axis for both transverse components (Algorithm 2), op 2 = CT along axis
  * twice (the pair of CT operators that meet in the middle of a step whose axis order ends
  * with that axis, Eq. "eq:L_sequence": one launch where the library has a two-pass kernel,
- * else two; the same result as op 1 applied twice).  Returns after the operator completed. */
+ * else two; the same result as op 1 applied twice), op 3 = the reverse L along z (CT along
+ * z, then the fluid sweep along z, Sect. 4.3) in one launch: FP32 contexts with plain FP32
+ * pressure recovery and a z axis of more than one cell only (MHD_ERR_INVALID otherwise); the
+ * same result as op 1 then op 0.  Returns after the operator completed. */
 mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt);
 
 /* c_max of the current state (Eq. "equat_CFL").  Blocking. */

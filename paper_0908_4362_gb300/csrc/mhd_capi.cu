@@ -148,6 +148,22 @@ static cudaError_t enqueue_ct2(mhd_ctx* ctx, int axis) {
   return e != cudaSuccess ? e : enqueue_ct<T>(ctx, axis);
 }
 
+// the reverse L along axis (CT, then fluid) in one launch; cudaErrorNotSupported (nothing
+// launched) where the library has no such kernel
+template <typename T>
+static cudaError_t enqueue_ct_fluid(mhd_ctx* ctx, int axis) {
+  FieldSet<T> in = fields_of<T>(ctx, false), out = fields_of<T>(ctx, true);
+  cudaError_t e;
+  {
+    ProfScope ps(ctx, 7);
+    e = Launch<T>::ct_fluid(ctx->g, in, out, ctx->cfg.gamma, ctx->cfg.h, ctx->ds, axis,
+                            ctx->cfg.fp64_pressure, ctx->stream);
+  }
+  if (e == cudaSuccess)
+    for (int k = 0; k < 8; ++k) ctx->cur[k] ^= 1;
+  return e;
+}
+
 template <typename T>
 static cudaError_t enqueue_step_t(mhd_ctx* ctx, int phase) {
   cudaError_t e;
@@ -543,7 +559,7 @@ mhd_status mhd_step(mhd_ctx* ctx, int nsteps, double t_end, int* steps_done, dou
 }
 
 mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt) {
-  if (!ctx || axis < 0 || axis > 2 || op < 0 || op > 2) return MHD_ERR_INVALID;
+  if (!ctx || axis < 0 || axis > 2 || op < 0 || op > 3) return MHD_ERR_INVALID;
   mhd_status s = sync_scalars(ctx);
   if (s != MHD_OK) return s;
   CK(cudaMemcpyAsync(&ctx->ds->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "dt");
@@ -551,7 +567,13 @@ mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt) {
   CK(cudaMemcpyAsync(&ctx->ds->dt_h, &dt_h, sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
      "dt/h");
   cudaError_t e;
-  if (ctx->esz == 4)
+  if (op == 3) {
+    e = ctx->esz == 4 ? enqueue_ct_fluid<float>(ctx, axis) : cudaErrorNotSupported;
+    if (e == cudaErrorNotSupported) {
+      ctx->err = "mhd_apply: no one-launch reverse L for this context and axis";
+      return MHD_ERR_INVALID;
+    }
+  } else if (ctx->esz == 4)
     e = op == 0 ? enqueue_fluid<float>(ctx, axis, false)
                 : op == 1 ? enqueue_ct<float>(ctx, axis) : enqueue_ct2<float>(ctx, axis);
   else

@@ -28,6 +28,12 @@ struct Launch {
   // x/y outside the shared-row form or with an outflow sweep axis)
   static cudaError_t ct2(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
                          double h, DevScalars* ds, int axis, cudaStream_t s);
+  // the reverse L along axis (CT, then the fluid sweep) in one launch; cudaErrorNotSupported
+  // where there is no such kernel (FP64, an axis other than z, a flat z axis, a pressure mode
+  // other than plain FP32)
+  static cudaError_t ct_fluid(const GridDesc& g, const FieldSet<T>& in, const FieldSet<T>& out,
+                              double gamma, double h, DevScalars* ds, int axis, int pm,
+                              cudaStream_t s);
   static cudaError_t cmax(const GridDesc& g, const FieldSet<T>& in, double gamma,
                           DevScalars* ds, int pm, cudaStream_t s);
   static cudaError_t dt(DevScalars* ds, double cfl_h, double h, cudaStream_t s);

@@ -332,6 +332,37 @@ static cudaError_t ct2_impl(const GridDesc& g, const FieldSet<T>& in, const Fiel
 }
 
 template <typename T>
+static cudaError_t ct_fluid_impl(const GridDesc& g, const FieldSet<T>& in,
+                                 const FieldSet<T>& out, double gamma, double h,
+                                 DevScalars* ds, int axis, int pm, cudaStream_t s) {
+  if constexpr (sizeof(T) != 4) {
+    return cudaErrorNotSupported;
+  } else {
+    if (axis != 2 || axis_is_flat(g, 2) || pm != PM_FP32) return cudaErrorNotSupported;
+    constexpr int Q = MHD_LOPZ_Q, L = MHD_CTZ_L;
+    const bool o32 = field_off32<float>(g), clamp = g.bc[2] == 1;
+    const float gm = (float)gamma;
+    dim3 grid;
+    if (seg_k_for(g.n[2]) == 2) {
+      constexpr int K = 2;
+      if (!ct_fluid_rows_z_grid<K>(g, Q, L, &grid)) return cudaErrorNotSupported;
+      if (clamp && o32) ct_fluid_rows_z<K, Q, PM_FP32, true, true><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+      else if (clamp) ct_fluid_rows_z<K, Q, PM_FP32, true, false><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+      else if (o32) ct_fluid_rows_z<K, Q, PM_FP32, false, true><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+      else ct_fluid_rows_z<K, Q, PM_FP32, false, false><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+      return cudaGetLastError();
+    }
+    constexpr int K = 3;
+    if (!ct_fluid_rows_z_grid<K>(g, Q, L, &grid)) return cudaErrorNotSupported;
+    if (clamp && o32) ct_fluid_rows_z<K, Q, PM_FP32, true, true><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+    else if (clamp) ct_fluid_rows_z<K, Q, PM_FP32, true, false><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+    else if (o32) ct_fluid_rows_z<K, Q, PM_FP32, false, true><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+    else ct_fluid_rows_z<K, Q, PM_FP32, false, false><<<grid, 32 * Q, 0, s>>>(g, in, out, gm, h, ds, L);
+    return cudaGetLastError();
+  }
+}
+
+template <typename T>
 static cudaError_t cmax_impl(const GridDesc& g, const FieldSet<T>& in, double gamma,
                              DevScalars* ds, int pm, cudaStream_t s) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -380,6 +411,11 @@ static cudaError_t convert(const S* src, D* dst, long long n, cudaStream_t s) {
   template <> cudaError_t Launch<T>::ct2(const GridDesc& g, const FieldSet<T>& in,          \
       const FieldSet<T>& out, double h, DevScalars* ds, int axis, cudaStream_t s) {         \
     return ct2_impl<T>(g, in, out, h, ds, axis, s);                                         \
+  }                                                                                         \
+  template <> cudaError_t Launch<T>::ct_fluid(const GridDesc& g, const FieldSet<T>& in,     \
+      const FieldSet<T>& out, double gamma, double h, DevScalars* ds, int axis, int pm,     \
+      cudaStream_t s) {                                                                     \
+    return ct_fluid_impl<T>(g, in, out, gamma, h, ds, axis, pm, s);                         \
   }                                                                                         \
   template <> cudaError_t Launch<T>::cmax(const GridDesc& g, const FieldSet<T>& in,         \
       double gamma, DevScalars* ds, int pm, cudaStream_t s) {                             \

@@ -154,6 +154,70 @@ __device__ __forceinline__ void seg_stage2(const V (&fr2)[K], const V (&fl2)[K],
   for (int i = 0; i < K; ++i) un[i] = Vec<V>::fnma(dth, Vec<V>::sub(g2[i], g2p[i]), u[i]);
 }
 
+// The two stages of the fluid sweep over a warp's window (Algorithm 1): u[K][5] the
+// conserved fluid variables of the lane's cells in local order (rho, m_n, m_t1, m_t2, E),
+// b[K][3] the cell-centred B (n, t1, t2); un the updated variables, valid on window cells
+// 3 .. 32K-4 when u and b are valid on the whole window.  Returns the status bits of the
+// flux evaluations at the window cells [v0, v1] (stage 1) and [v0 + 1, v1 - 1] (stage 2),
+// the cells whose operands are real (v0 = 0, v1 = 32K - 1 where u and b are valid
+// everywhere).
+template <typename T, int PM, int K>
+__device__ __forceinline__ int fluid_seg_core(const T (&u)[K][5], const T (&b)[K][3], T gamma,
+                                              T dth, T hd, int lane, int v0, int v1,
+                                              T (&un)[K][5]) {
+  int st = 0;
+  // stage 1: first-order fluxes, half step
+  T uh[K][5];
+  {
+    T fr[5][K], fl[5][K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      T a[5], c[5];
+      const int s1 = cell_flux<T, PM>(u[i], b[i], gamma, a, c);
+      const int w1 = lane * K + i;
+      if (w1 >= v0 && w1 <= v1) st |= s1;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) { fr[q][i] = a[q]; fl[q][i] = c[q]; }
+    }
+    T uq[5][K], uhq[5][K];
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int i = 0; i < K; ++i) uq[q][i] = u[i][q];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) seg_stage1<T, K>(fr[q], fl[q], uq[q], hd, uhq[q]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int i = 0; i < K; ++i) uh[i][q] = uhq[q][i];
+  }
+  // stage 2: limited fluxes of u^{t+dt/2}, full update
+  {
+    T fr2[5][K], fl2[5][K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      T a[5], c[5];
+      const int s2 = cell_flux<T, PM>(uh[i], b[i], gamma, a, c);
+      const int w = lane * K + i;
+      if (w >= v0 + 1 && w <= v1 - 1) st |= s2;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) { fr2[q][i] = a[q]; fl2[q][i] = c[q]; }
+    }
+    T uq[5][K], unq[5][K];
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int i = 0; i < K; ++i) uq[q][i] = u[i][q];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) seg_stage2<T, K>(fr2[q], fl2[q], uq[q], dth, unq[q]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int i = 0; i < K; ++i) un[i][q] = unq[q][i];
+  }
+  return st;
+}
+
 // one warp: window `wid` (seg_place); all 32 lanes call it
 template <typename T, bool LAST, int PM, int K, bool NC, bool OFF32 = false>
 __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldSet<T>& in,
@@ -191,54 +255,8 @@ __device__ __forceinline__ void fluid_seg_z_warp(const GridDesc& g, const FieldS
     b[i][1] = T(0.5) * (ldx<NC>(AD::at(in.f[5], c)) + ldx<NC>(AD::at(in.f[5], r1 + zc)));
     b[i][2] = T(0.5) * (ldx<NC>(AD::at(in.f[6], c)) + ldx<NC>(AD::at(in.f[6], r2 + zc)));
   }
-  // stage 1: first-order fluxes, half step
-  T uh[K][5];
-  {
-    T fr[5][K], fl[5][K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      T a[5], c[5];
-      st |= cell_flux<T, PM>(u[i], b[i], gamma, a, c);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) { fr[q][i] = a[q]; fl[q][i] = c[q]; }
-    }
-    T uq[5][K], uhq[5][K];
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-#pragma unroll
-      for (int i = 0; i < K; ++i) uq[q][i] = u[i][q];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) seg_stage1<T, K>(fr[q], fl[q], uq[q], hd, uhq[q]);
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-#pragma unroll
-      for (int i = 0; i < K; ++i) uh[i][q] = uhq[q][i];
-  }
-  // stage 2: limited fluxes of u^{t+dt/2}, full update
   T un[K][5];
-  {
-    T fr2[5][K], fl2[5][K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      T a[5], c[5];
-      const int s2 = cell_flux<T, PM>(uh[i], b[i], gamma, a, c);
-      const int w = lane * K + i;                          // window cell, 1 .. 32K-2 valid
-      if (w >= 1 && w <= 32 * K - 2) st |= s2;
-#pragma unroll
-      for (int q = 0; q < 5; ++q) { fr2[q][i] = a[q]; fl2[q][i] = c[q]; }
-    }
-    T uq[5][K], unq[5][K];
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-#pragma unroll
-      for (int i = 0; i < K; ++i) uq[q][i] = u[i][q];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) seg_stage2<T, K>(fr2[q], fl2[q], uq[q], dth, unq[q]);
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-#pragma unroll
-      for (int i = 0; i < K; ++i) un[i][q] = unq[q][i];
-  }
+  st |= fluid_seg_core<T, PM, K>(u, b, gamma, dth, hd, lane, 0, 32 * K - 1, un);
   T cm = T(0);
   bool nan_seen = false;
 #pragma unroll
@@ -564,13 +582,19 @@ ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) 
 #define MHD_CTZ_ROWS 1
 #endif
 #ifndef MHD_CTZ_Q
-#define MHD_CTZ_Q 16
+#define MHD_CTZ_Q 8
 #endif
 #ifndef MHD_CTZ_L
-#define MHD_CTZ_L 32
+#define MHD_CTZ_L 16
 #endif
-// resident blocks asked of the compiler: a 64-register cap (32 / Q blocks of Q warps per SM)
-template <int Q> struct CtRowsZMinBlocks { static constexpr int value = Q <= 32 ? 32 / Q : 1; };
+// resident blocks asked of the compiler: by default a 64-register cap (32 / Q blocks of Q
+// warps per SM)
+#ifndef MHD_CTZ_MINB
+#define MHD_CTZ_MINB 0
+#endif
+template <int Q> struct CtRowsZMinBlocks {
+  static constexpr int value = MHD_CTZ_MINB > 0 ? MHD_CTZ_MINB : (Q <= 32 ? 32 / Q : 1);
+};
 
 template <int K, int Q, int PASSES = 1, bool CLAMPZ = false, bool OFF32 = false>
 __global__ void __launch_bounds__(32 * Q, CtRowsZMinBlocks<Q>::value)
@@ -719,6 +743,207 @@ ct_rows_z(GridDesc g, FieldSet<float> in, FieldSet<float> out, double h, DevScal
 template <int K, int PASSES>
 __host__ inline bool ct_rows_z_grid(const GridDesc& g, int Q, int L, dim3* grid) {
   constexpr int SEG = 32 * K - 8 * PASSES;
+  const long long gx = (g.n[1] + Q - 2) / (Q - 1), gy = (g.n[2] + SEG - 1) / SEG,
+                  gz = (g.n[0] + L - 1) / L;
+  if (gx > 0x7FFFFFFFll || gy > 65535 || gz > 65535) return false;
+  *grid = dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
+  return true;
+}
+
+
+// ------------------------------------------------------------------------------------
+// The reverse z operator L_z (CT_z, then fluid_z) in one launch, FP32: ct_fluid_rows_z.
+//
+// The march of ct_rows_z, with the fluid sweep of each pencil run as soon as the B it
+// needs is final: the fluid of row r needs the advected B_x of its own and of the next row
+// (its cell-centred B_x), the advected B_y of its own and of the upper y row (the warp above,
+// through shared memory), and B_z, whose constraint completes with the x-face EMF of row r + 1.
+// So in iteration r a warp runs the CT of row r and then the fluid of row r - 1, whose rho
+// and m_z it loaded as CT operands one iteration earlier.  Unlike the forward order (fluid,
+// then CT), no pencil's fluid is evaluated twice across x or y: the face velocities come from
+// the input state.  The window pays instead: the fluid's stencil reaches 3 cells and B_z the
+// CT's 4, so a window of 32K cells updates 32K - 14 (against 32K - 6 and 32K - 8 for the two
+// operators apart).  Every value is the same operation on the same operands as ct_seg_z
+// followed by fluid_seg_z (ghost cells of an outflow z axis re-clamped to their edge cells,
+// as the fluid's clamped loads of the CT's output would read them), so the result is the same
+// bits.  Not the last sweep of a step (no c_max reduction).
+// ------------------------------------------------------------------------------------
+#ifndef MHD_LOPZ_Q
+#define MHD_LOPZ_Q 8
+#endif
+#ifndef MHD_LOPZ_MINB
+#define MHD_LOPZ_MINB 2
+#endif
+
+template <int K, int Q, int PM, bool CLAMPZ = false, bool OFF32 = false>
+__global__ void __launch_bounds__(32 * Q, MHD_LOPZ_MINB)
+ct_fluid_rows_z(GridDesc g, FieldSet<float> in, FieldSet<float> out, float gamma, double h,
+                DevScalars* ds, int L) {
+  using AD = FieldAddr<float, OFF32>;
+  using I = typename AD::I;
+  constexpr int HL = 7, W = 32 * K, SEG = W - 14;
+  __shared__ float se[2][Q][W];   // y-face EMF of each warp's own pipeline
+  __shared__ float sb[2][Q][W];   // advected B_y of each warp's pencil (the lower warp's fluid)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int bcx = g.bc[0], bcy = g.bc[1], bcz = g.bc[2];
+  const int yw = (int)blockIdx.x * (Q - 1) + w;
+  const int s0 = (int)blockIdx.y * SEG;
+  const int xb = (int)blockIdx.z * L;
+  const int xe = min(xb + L, nx);
+  const int y = wrap_index(yw, ny, bcy), ylo = wrap_index(y - 1, ny, bcy);
+  const int yup = wrap_index(y + 1, ny, bcy);
+  const bool y_edge = wrap_index(yup - 1, ny, bcy) != y;   // upper EMF row = own
+  const bool y_self = yup == y;                             // upper B_y row = own
+  const bool writer = w < Q - 1 && yw < ny;
+  const int wn = w + 1 < Q ? w + 1 : w;
+  const bool x_edge = xe == nx && bcx == 1;
+  const float dts = step_factor<float>(ds, h);
+  const float2 ndth2 = splat2(-dts * kEmf2Inv), nhd2 = splat2(-(0.5f * dts) * kEmf2Inv);
+  const float dc = dts * kEmf2Inv;
+  const float fdth = dts * float(FluxScale<float>::inv), fhd = 0.5f * fdth;
+  const int z0 = s0 - HL + lane * K;
+  I zc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) zc[i] = AD::of(wrap_index(z0 + i, nz, bcz));
+  const I ys = AD::of((long long)y * g.s[1]), ylos = AD::of((long long)ylo * g.s[1]);
+  float rp[K], mp[K];
+  {
+    const I row = AD::of((long long)wrap_index(xb - 1, nx, bcx) * g.s[0]) + ys;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      rp[i] = __ldg(AD::at(in.f[0], row + zc[i]));
+      mp[i] = __ldg(AD::at(in.f[3], row + zc[i]));
+    }
+  }
+  // carried from row r - 1: B_z, x-face EMF, y-face EMF difference (the constraint), the
+  // advected B_x and B_y of the pencil and B_y of the upper y row (the fluid's cell-centred B)
+  float bap[K], e1p[K], d2p[K], bxp[K], byp[K], byu[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) bap[i] = e1p[i] = d2p[i] = bxp[i] = byp[i] = byu[i] = 0.f;
+  I xop = 0;
+  int st = 0;
+  bool outc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int wc = lane * K + i;
+    outc[i] = writer && wc >= HL && wc < HL + SEG && z0 + i < nz;
+  }
+  // B_z of row r - 1 (stored), then its fluid sweep; en1: x-face EMF of the upper x row,
+  // bxu: advected B_x of the upper x row
+  auto finish_row = [&](const float (&en1)[K], const float (&bxu)[K]) {
+    float bz[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      float b = ffma(dc, en1[i] - e1p[i], bap[i]);   // constraint from t1 = x, then t2 = y
+      bz[i] = ffma(dc, d2p[i], b);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (outc[i]) {
+        *AD::at(out.f[7], xop + ys + AD::of(z0 + i)) = bz[i];
+        if (!(bz[i] == bz[i])) st |= ST_NONFINITE;
+      }
+    if (CLAMPZ) reclamp_window<float, K>(bz, s0 - HL, z0, nz);
+    float bzn[K];
+    next_cell<float, K>(bz, bzn);
+    float u[K][5], bb[K][3], un[K][5];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const I c = xop + ys + zc[i];
+      u[i][0] = rp[i];
+      u[i][1] = mp[i];
+      u[i][2] = __ldg(AD::at(in.f[1], c));
+      u[i][3] = __ldg(AD::at(in.f[2], c));
+      u[i][4] = __ldg(AD::at(in.f[4], c));
+      bb[i][0] = 0.5f * (bz[i] + bzn[i]);
+      bb[i][1] = 0.5f * (bxp[i] + bxu[i]);
+      bb[i][2] = 0.5f * (byp[i] + byu[i]);
+    }
+    // the CT's output, hence the cell-centred B, is valid on window cells 4 .. 32K-5
+    st |= fluid_seg_core<float, PM, K>(u, bb, gamma, fdth, fhd, lane, 4, W - 5, un);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (outc[i]) {
+        const I co = xop + ys + AD::of(z0 + i);
+        *AD::at(out.f[0], co) = un[i][0];
+        *AD::at(out.f[3], co) = un[i][1];
+        *AD::at(out.f[1], co) = un[i][2];
+        *AD::at(out.f[2], co) = un[i][3];
+        *AD::at(out.f[4], co) = un[i][4];
+        if (!(un[i][0] > 0.f)) st |= ST_UNPHYSICAL;
+      }
+  };
+  const int rlast = x_edge ? xe - 1 : xe;
+  for (int r = xb; r <= rlast; ++r) {
+    const I xo = AD::of((long long)wrap_index(r, nx, bcx) * g.s[0]);
+    const I row = xo + ys, rowlo = xo + ylos;
+    float r0[K], m0[K], bz[K];
+    float2 vo[K], bo[K], eo[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const I c = row + zc[i], cl = rowlo + zc[i];
+      r0[i] = __ldg(AD::at(in.f[0], c));
+      m0[i] = __ldg(AD::at(in.f[3], c));
+      const float rl = __ldg(AD::at(in.f[0], cl)), ml = __ldg(AD::at(in.f[3], cl));
+      bo[i] = make_float2(__ldg(AD::at(in.f[5], c)), __ldg(AD::at(in.f[6], c)));
+      bz[i] = __ldg(AD::at(in.f[7], c));
+      vo[i] = make_float2(Num<float>::div(m0[i] + mp[i], r0[i] + rp[i]),
+                          Num<float>::div(m0[i] + ml, r0[i] + rl));
+    }
+    emf_seg2<K>(vo, bo, ndth2, nhd2, eo);
+    if (CLAMPZ) reclamp_window<float2, K>(bo, s0 - HL, z0, nz);
+    if (r > xb) {
+      float en1[K], bxu[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) { en1[i] = eo[i].x; bxu[i] = bo[i].x; }
+      finish_row(en1, bxu);
+    }
+    if (r < xe) {
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (outc[i]) {
+          const I co = row + AD::of(z0 + i);
+          *AD::at(out.f[5], co) = bo[i].x;
+          *AD::at(out.f[6], co) = bo[i].y;
+          if (!(bo[i].x == bo[i].x) || !(bo[i].y == bo[i].y)) st |= ST_NONFINITE;
+        }
+      float(&swe)[Q][W] = se[r & 1];
+      float(&swb)[Q][W] = sb[r & 1];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        swe[w][lane * K + i] = eo[i].y;
+        swb[w][lane * K + i] = bo[i].y;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const float en2 = y_edge ? eo[i].y : swe[wn][lane * K + i];
+        d2p[i] = en2 - eo[i].y;
+        e1p[i] = eo[i].x;
+        byu[i] = y_self ? bo[i].y : swb[wn][lane * K + i];
+        bap[i] = bz[i];
+        bxp[i] = bo[i].x;
+        byp[i] = bo[i].y;
+      }
+      xop = xo;
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) { rp[i] = r0[i]; mp[i] = m0[i]; }
+  }
+  if (x_edge) {
+    // the last row: its upper x row is itself (outflow), for the EMF and for B_x
+    float en1[K], bxu[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) { en1[i] = e1p[i]; bxu[i] = bxp[i]; }
+    finish_row(en1, bxu);
+  }
+  if (st) atomicOr(&ds->status, st);
+}
+
+template <int K>
+__host__ inline bool ct_fluid_rows_z_grid(const GridDesc& g, int Q, int L, dim3* grid) {
+  constexpr int SEG = 32 * K - 14;
   const long long gx = (g.n[1] + Q - 2) / (Q - 1), gy = (g.n[2] + SEG - 1) / SEG,
                   gz = (g.n[0] + L - 1) / L;
   if (gx > 0x7FFFFFFFll || gy > 65535 || gz > 65535) return false;

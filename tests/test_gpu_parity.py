@@ -449,3 +449,38 @@ def test_ct_z_rows_same_bits_as_segments(mhd, monkeypatch, case, op):
             got.append(s.read())
     monkeypatch.delenv("MHD_CTZ_SEG")
     assert np.array_equal(got[0], got[1]), np.abs(got[0] - got[1]).max()
+
+
+@pytest.mark.parametrize("case", CTZ_FORM_CASES, ids=[c[0] for c in CTZ_FORM_CASES])
+def test_reverse_lz_in_one_launch(mhd, case):
+    """The reverse z operator L_z (CT along z, then the fluid sweep along z) in one launch
+    (mhd_apply op 3, FP32): the same bits as the two launches (op 1, then op 0), over the
+    shapes and boundaries of the CT form test, and within tolerance of the oracle's CT_z then
+    fluid_z."""
+    prob = case[1]()
+    ref = oracle.Oracle.from_problem(prob)
+    dt = 0.5 * ref.dt()
+    ref.ct(2, dt)
+    ref.fluid(2, dt)
+    got = []
+    for ops in ((1, 0), (3,)):
+        with mhd.Solver.from_problem(prob, prec=mhd.FP32) as s:
+            for op in ops:
+                s.apply(op, 2, dt)
+            got.append(s.read())
+    assert np.array_equal(got[0], got[1]), np.abs(got[0] - got[1]).max()
+    err = rel_l1(got[1], ref.f)
+    assert np.all(err <= 4e-6), err
+
+
+def test_reverse_lz_one_launch_rejected_where_absent(mhd):
+    """op 3 exists for FP32 contexts with plain FP32 pressure recovery only: FP64 contexts
+    and the other pressure modes get MHD_ERR_INVALID, and their state is left as it was."""
+    prob = I.random_smooth((6, 5, 40), seed=43)
+    for kw in ({"prec": mhd.FP64}, {"prec": mhd.FP32, "pressure": mhd.PRESSURE_FP64}):
+        with mhd.Solver.from_problem(prob, **kw) as s:
+            before = s.read()
+            with pytest.raises(mhd.MhdError) as e:
+                s.apply(3, 2, 1e-3)
+            assert e.value.status == mhd.MHD_ERR_INVALID
+            assert np.array_equal(s.read(), before)
