@@ -592,12 +592,16 @@ ct_seg_z(GridDesc g, FieldSet<T> in, FieldSet<T> out, double h, DevScalars* ds) 
 #ifndef MHD_CTZ_MINB
 #define MHD_CTZ_MINB 0
 #endif
-template <int Q> struct CtRowsZMinBlocks {
-  static constexpr int value = MHD_CTZ_MINB > 0 ? MHD_CTZ_MINB : (Q <= 32 ? 32 / Q : 1);
+#ifndef MHD_CTZ2_MINB
+#define MHD_CTZ2_MINB 0
+#endif
+template <int Q, int PASSES> struct CtRowsZMinBlocks {
+  static constexpr int m = PASSES == 2 ? MHD_CTZ2_MINB : MHD_CTZ_MINB;
+  static constexpr int value = m > 0 ? m : (Q <= 32 ? 32 / Q : 1);
 };
 
 template <int K, int Q, int PASSES = 1, bool CLAMPZ = false, bool OFF32 = false>
-__global__ void __launch_bounds__(32 * Q, CtRowsZMinBlocks<Q>::value)
+__global__ void __launch_bounds__(32 * Q, CtRowsZMinBlocks<Q, PASSES>::value)
 ct_rows_z(GridDesc g, FieldSet<float> in, FieldSet<float> out, double h, DevScalars* ds, int L) {
   using AD = FieldAddr<float, OFF32>;
   using I = typename AD::I;
