@@ -45,7 +45,8 @@ STEP_ALG_BYTES = 384
 # DRAM bytes per cell of one fluid-sweep launch (average over the 4 x/y and 2 z launches of
 # a step) from ncu captures on a 256^3 grid (the ncu summaries under profiles/), keyed by the
 # hash of the kernel sources they were taken on; another hash reports null.
-NCU_TRAFFIC_PER_CELL = {"6493be2955de5ac4": 50.74, "b10257c0c22a2f1c": 50.74}
+NCU_TRAFFIC_PER_CELL = {"6493be2955de5ac4": 50.74, "b10257c0c22a2f1c": 50.74,
+                        "e5f6604cfb2b726c": 50.74}
 # thread instructions per cell of one launch of each sweep kernel (ncu
 # smsp__thread_inst_executed.sum / cells, 256^3; one launch in six of each axis's fluid sweeps
 # also reduces c_max, and one CT launch in five of each axis is a two-pass middle pair: both
@@ -54,7 +55,9 @@ NCU_TRAFFIC_PER_CELL = {"6493be2955de5ac4": 50.74, "b10257c0c22a2f1c": 50.74}
 NCU_INSTR_PER_CELL = {"6493be2955de5ac4": {"fluid_x": 313.3, "fluid_y": 313.3, "fluid_z": 364.9,
                                            "ct_x": 178.4, "ct_y": 178.4, "ct_z": 263.8},
                       "b10257c0c22a2f1c": {"fluid_x": 313.3, "fluid_y": 313.3, "fluid_z": 364.9,
-                                           "ct_x": 197.3, "ct_y": 197.3, "ct_z": 189.2}}
+                                           "ct_x": 197.3, "ct_y": 197.3, "ct_z": 189.2},
+                      "e5f6604cfb2b726c": {"fluid_x": 313.3, "fluid_y": 313.3, "fluid_z": 364.9,
+                                           "ct_x": 197.3, "ct_y": 197.3, "ct_z": 190.4}}
 
 
 KERNEL_SOURCES = ("mhd_kernels.cuh", "mhd_march.cuh", "mhd_segz.cuh", "mhd_flat.cuh",
