@@ -96,9 +96,10 @@ mhd_status mhd_step(mhd_ctx* ctx, int nsteps, double t_end, int* steps_done, dou
  * twice (the pair of CT operators that meet in the middle of a step whose axis order ends
  * with that axis, Eq. "eq:L_sequence": one launch where the library has a two-pass kernel,
  * else two; the same result as op 1 applied twice), op 3 = the reverse L along z (CT along
- * z, then the fluid sweep along z, Sect. 4.3) in one launch: FP32 contexts with plain FP32
- * pressure recovery and a z axis of more than one cell only (MHD_ERR_INVALID otherwise); the
- * same result as op 1 then op 0.  Returns after the operator completed. */
+ * z, then the fluid sweep along z, Sect. 4.3) in one launch: axis 2, FP32 contexts with
+ * plain FP32 pressure recovery and a z axis of more than one cell only (MHD_ERR_INVALID
+ * otherwise, the state left as it was); the same result as op 1 then op 0, measured slower
+ * than those two launches and not used by mhd_step.  Returns after the operator completed. */
 mhd_status mhd_apply(mhd_ctx* ctx, int op, int axis, double dt);
 
 /* c_max of the current state (Eq. "equat_CFL").  Blocking. */
