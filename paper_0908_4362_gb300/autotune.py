@@ -23,14 +23,15 @@ from . import build as _build
 from . import mhd
 
 CACHE = os.path.join(_build.BUILD, "autotune.json")
-VERSION = 2
+VERSION = 3
 
 # per-class knobs and their candidates, in tuning order ("alone" only for classes of at
-# least ALONE_MIN_CELLS cells per grid: smaller grids leave most of the GPU idle alone)
+# least ALONE_MIN_CELLS cells per grid on average: smaller grids leave most of the GPU idle
+# alone)
 KNOBS = (("alone", (0, 1)), ("march_len", (192, 128, 256)), ("ct_march", (0, 1)),
          ("seg_k", (0, 2, 3)), ("z_warps", (0, 32, 128)))
 DEFAULTS = {"alone": 0, "march_len": 192, "ct_march": 0, "seg_k": 0, "z_warps": 0}
-ALONE_MIN_CELLS = 1 << 21
+ALONE_MIN_CELLS = 1 << 19
 THREADS = (128, 256)
 MIN_GAIN = 0.01          # a candidate replaces the best so far when at least 1% faster
 
