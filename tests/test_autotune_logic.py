@@ -39,6 +39,8 @@ def fake_gpu(monkeypatch, tmp_path):
         c = prob.ncells * 1e-9
         if big and shape.get("alone"):
             c *= 0.5                       # large grids: the single-grid route halves the cost
+        if not big and shape.get("alone"):
+            c *= 1.1                       # mid-size grids: the route is tried, and loses
         if not big and shape.get("ct_march"):
             c *= 0.995                     # below the 1% threshold: must not be taken
         if not big and shape.get("march_len") == 256:
@@ -97,17 +99,21 @@ def fake_gpu(monkeypatch, tmp_path):
 
 
 def test_tune_batch_descent(fake_gpu):
-    probs = [FakeProblem((256, 256, 256))] + [FakeProblem((60, 60, 60))] * 40
+    probs = ([FakeProblem((256, 256, 256))] + [FakeProblem((60, 60, 60))] * 40 +
+             [FakeProblem((96, 96, 96))] * 4)
     res = autotune.tune_batch(probs, nsteps=3, repeats=2)
     assert res["threads_per_cta"] == 128
     big, small = autotune.shape_class((256, 256, 256)), autotune.shape_class((60, 60, 60))
+    mid = autotune.shape_class((96, 96, 96))
     assert res["classes"][big] == {"alone": 1}           # no tile shapes once routed alone
     assert res["classes"][small] == {"march_len": 256}   # 10% taken, 0.5% (ct_march) not
     assert "alone" not in res["classes"][small]          # small grids never try the route
+    assert "alone" not in res["classes"][mid]            # tried (below), slower, not taken
     assert res["tuned_ms"] < res["default_ms"]
     tried = [cfg for cfg in fake_gpu["configs"]]
-    assert not any(sh.get("alone") for _, shapes in tried for p, sh in zip(probs, shapes)
-                   if p.ncells < 1 << 21)
+    routed = {p.n for _, shapes in tried for p, sh in zip(probs, shapes) if sh.get("alone")}
+    assert routed == {(256, 256, 256), (96, 96, 96)}     # the route is offered from 2^19 cells
+    assert 60 ** 3 < autotune.ALONE_MIN_CELLS <= 96 ** 3
     # the result is cached: a second call configures nothing
     n = len(fake_gpu["configs"])
     assert autotune.tune_batch(probs, nsteps=3, repeats=2) == res
