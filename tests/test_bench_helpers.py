@@ -36,3 +36,16 @@ def test_rel_l1_fields_groups_vector_components():
     assert abs(err[3] - 50e-3 / den_m) < 1e-12
     assert abs(err[0] - 100e-3 / np.abs(b[0]).sum()) < 1e-12
     assert err[5] == err[6] == err[7] == 0.0
+
+
+def test_ncu_constants_cover_the_current_kernel_sources():
+    """The roofline's DRAM traffic and the issue object come from ncu counts keyed by the
+    hash of the kernel sources they were taken on; the sources as committed must have them
+    (a kernel edit without fresh counts would report traffic as null)."""
+    h = bench.kernel_source_hash()
+    assert h in bench.NCU_TRAFFIC_PER_CELL, h
+    assert h in bench.NCU_INSTR_PER_CELL, h
+    ipc = bench.NCU_INSTR_PER_CELL[h]
+    assert set(ipc) == {"fluid_x", "fluid_y", "fluid_z", "ct_x", "ct_y", "ct_z"}
+    # the fluid sweeps move about their algorithmic bytes per cell
+    assert 0.9 * bench.ALG_BYTES["fluid"] <= bench.NCU_TRAFFIC_PER_CELL[h] <= 1.1 * bench.ALG_BYTES["fluid"]
